@@ -1,0 +1,215 @@
+"""Seeded synthetic inputs for the D3V15 FD-LB solver.
+
+This module holds the workloads only: grids, model constants, boundary kinds
+and initial macroscopic fields (rho, u, T), plus seeded random perturbations
+and request traces.  It contains none of the lattice Boltzmann arithmetic
+(no equilibrium, moments or fluxes), so both the CUDA path and the CPU oracle
+may take their inputs from it.
+
+Conventions: R = 1 (so T = p / rho), gamma = 1.4, cell-centred nodes
+x = (i + 1/2) dx on [0, nx dx), fields shaped [nz, ny, nx] and u [3, nz, ny, nx].
+Boundary kinds: 0 periodic, 1 fixed, 2 extrapolate, 3 reflect.
+Tuples of states are (rho, u1, u2, u3, T) as in the paper's Sec. 4.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+PERIODIC, FIXED, EXTRAPOLATE, REFLECT = 0, 1, 2, 3
+GAMMA = 1.4
+
+
+def rankine_hugoniot(mach: float, rho1: float = 1.0, p1: float = 1.0, gamma: float = GAMMA):
+    """Post-shock (rho2, u2, p2) and shock speed D of a normal shock of Mach
+    number ``mach`` moving in +x into gas at rest (rho1, p1)."""
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    a1 = math.sqrt(gamma * p1 / rho1)
+    D = mach * a1
+    u2 = D * (1.0 - rho1 / rho2)
+    return rho2, u2, p2, D
+
+
+def state_from_p(rho, u1, u2, u3, p):
+    """(rho, u1, u2, u3, T) with T = p / rho (R = 1)."""
+    return (rho, u1, u2, u3, p / rho)
+
+
+@dataclasses.dataclass
+class Workload:
+    """One solver run: grid, constants, boundaries and initial fields."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    c1: float
+    c2: float
+    eta0: float
+    dt: float
+    tau: float
+    steps: int
+    gamma: float = GAMMA
+    bc_lo: tuple = (PERIODIC, PERIODIC, PERIODIC)
+    bc_hi: tuple = (PERIODIC, PERIODIC, PERIODIC)
+    fixed_lo: tuple = ((0.0,) * 5,) * 3
+    fixed_hi: tuple = ((0.0,) * 5,) * 3
+    ic: object = None  # callable(workload) -> (rho, u, T)
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def initial_fields(self):
+        return self.ic(self)
+
+    def with_grid(self, nx, ny, nz, dx=None):
+        """Same physics on another grid (dx defaults to the same domain length in x)."""
+        d = dataclasses.replace(self, nx=nx, ny=ny, nz=nz, dx=dx if dx is not None else self.dx * self.nx / nx)
+        return d
+
+
+def cell_centres(n: int, dx: float) -> np.ndarray:
+    return (np.arange(n, dtype=np.float64) + 0.5) * dx
+
+
+def _two_state_x(w: Workload, left, right, x0: float):
+    x = cell_centres(w.nx, w.dx)
+    L = np.asarray(left, dtype=np.float64)
+    R = np.asarray(right, dtype=np.float64)
+    sel = (x < x0)[None, None, :]
+    shape = (w.nz, w.ny, w.nx)
+    rho = np.where(sel, L[0], R[0]) * np.ones(shape)
+    u = np.stack([np.where(sel, L[1 + a], R[1 + a]) * np.ones(shape) for a in range(3)])
+    T = np.where(sel, L[4], R[4]) * np.ones(shape)
+    return rho, u, T
+
+
+def shock_tube(name, nx, ny, nz, dx, left, right, x0, c1, c2, eta0, dt, tau, steps, gamma=GAMMA):
+    """Riemann problem along x, periodic in y and z, x faces held at the
+    initial left/right states (no wave reaches them before the end time)."""
+    w = Workload(name=name, nx=nx, ny=ny, nz=nz, dx=dx, c1=c1, c2=c2, eta0=eta0, dt=dt, tau=tau,
+                 steps=steps, gamma=gamma,
+                 bc_lo=(FIXED, PERIODIC, PERIODIC), bc_hi=(FIXED, PERIODIC, PERIODIC),
+                 fixed_lo=(tuple(left), (0.0,) * 5, (0.0,) * 5),
+                 fixed_hi=(tuple(right), (0.0,) * 5, (0.0,) * 5),
+                 meta={"left": tuple(left), "right": tuple(right), "x0": x0})
+    w.ic = _tube_ic
+    return w
+
+
+def _tube_ic(w: Workload):
+    return _two_state_x(w, w.meta["left"], w.meta["right"], w.meta["x0"])
+
+
+def _sphere_ic(w: Workload):
+    amb = np.asarray(w.meta["ambient"], dtype=np.float64)
+    sph = np.asarray(w.meta["sphere"], dtype=np.float64)
+    cx, cy, cz = w.meta["centre"]
+    R = w.meta["radius"]
+    x = cell_centres(w.nx, w.dx)
+    y = cell_centres(w.ny, w.dx)
+    z = cell_centres(w.nz, w.dx)
+    r2 = (x[None, None, :] - cx) ** 2 + (y[None, :, None] - cy) ** 2 + (z[:, None, None] - cz) ** 2
+    inside = r2 <= R * R
+    shape = (w.nz, w.ny, w.nx)
+    rho = np.where(inside, sph[0], amb[0]) * np.ones(shape)
+    u = np.stack([np.where(inside, sph[1 + a], amb[1 + a]) * np.ones(shape) for a in range(3)])
+    T = np.where(inside, sph[4], amb[4]) * np.ones(shape)
+    return rho, u, T
+
+
+def shock_sphere(name, nx, ny, nz, dx, mach, sphere_rho, radius, centre, c1, c2, eta0, dt, tau, steps,
+                 ambient_rho=1.0, ambient_p=1.0, gamma=GAMMA):
+    """Planar shock entering at x = 0 into gas at rest holding a sphere of
+    another density at the same pressure.  The domain starts all pre-shock;
+    the x-lo boundary layers hold the post-shock state, so the boundary
+    Riemann problem is exactly the shock of the given Mach number.  x-hi
+    extrapolates, y and z are periodic.  Sphere membership: cell centre
+    within the radius (sharp)."""
+    rho2, u2, p2, D = rankine_hugoniot(mach, ambient_rho, ambient_p, gamma)
+    post = state_from_p(rho2, u2, 0.0, 0.0, p2)
+    amb = state_from_p(ambient_rho, 0.0, 0.0, 0.0, ambient_p)
+    sph = state_from_p(sphere_rho, 0.0, 0.0, 0.0, ambient_p)
+    w = Workload(name=name, nx=nx, ny=ny, nz=nz, dx=dx, c1=c1, c2=c2, eta0=eta0, dt=dt, tau=tau,
+                 steps=steps, gamma=gamma,
+                 bc_lo=(FIXED, PERIODIC, PERIODIC), bc_hi=(EXTRAPOLATE, PERIODIC, PERIODIC),
+                 fixed_lo=(post, (0.0,) * 5, (0.0,) * 5),
+                 meta={"ambient": amb, "sphere": sph, "post": post, "centre": tuple(centre),
+                       "radius": radius, "mach": mach, "shock_speed": D})
+    w.ic = _sphere_ic
+    return w
+
+
+# ---------------------------------------------------------------- the workloads
+
+LAX_LEFT = state_from_p(0.445, 0.698, 0.0, 0.0, 3.528)
+LAX_RIGHT = state_from_p(0.5, 0.0, 0.0, 0.0, 0.571)
+HM_LEFT = state_from_p(5.0, 0.0, 0.0, 0.0, 500.0)
+HM_RIGHT = state_from_p(1.0, 0.0, 0.0, 0.0, 1.0)
+
+
+def lax_tube(nx=200, ny=4, nz=4):
+    """Lax shock tube: 200x4x4 on [0,1], dx = 0.005, dt = tau = 2e-5, 7000
+    steps to t = 0.14, (c1, c2, eta0) = (2, 6, 2) as in the paper's Lax run."""
+    return shock_tube("lax_tube_200x4x4", nx, ny, nz, 1.0 / nx, LAX_LEFT, LAX_RIGHT, 0.5,
+                      2.0, 6.0, 2.0, 2e-5, 2e-5, 7000)
+
+
+def high_mach_tube(nx=2000, ny=4, nz=4):
+    """High-Mach tube: 2000x4x4 on [0,1], dx = 5e-4, left (5, 0, p=500),
+    right (1, 0, p=1); (c1, c2, eta0) = (12, 36, 20), dt = tau = 2e-6, run
+    until the shock reaches x = 0.9 (15,980 steps)."""
+    return shock_tube("high_mach_tube_2000x4x4", nx, ny, nz, 1.0 / nx, HM_LEFT, HM_RIGHT, 0.5,
+                      12.0, 36.0, 20.0, 2e-6, 2e-6, 15980)
+
+
+def shock_droplet(n=256):
+    """Mach-2 shock into a rho = 5 droplet (radius 0.1, centre (0.3, 0.5, 0.5))
+    on the unit cube, n^3 cells; (c1, c2, eta0) = (2, 6, 4), dt = tau = 5e-5,
+    2000 steps."""
+    return shock_sphere(f"shock_droplet_{n}^3", n, n, n, 1.0 / n, 2.0, 5.0, 0.1, (0.3, 0.5, 0.5),
+                        2.0, 6.0, 4.0, 5e-5, 5e-5, 2000)
+
+
+def shock_bubble(nx=512, ny=256, nz=256, mach=3.0):
+    """Mach-3 shock into a rho = 0.1 bubble (radius 0.15, centre (0.35, 0.5,
+    0.5)), 512x256x256 cells of 1/256; (c1, c2, eta0) = (4, 12, 8), dt = tau = 2e-5."""
+    dx = 1.0 / ny
+    return shock_sphere(f"shock_bubble_{nx}x{ny}x{nz}", nx, ny, nz, dx, mach, 0.1, 0.15, (0.35, 0.5, 0.5),
+                        4.0, 12.0, 8.0, 2e-5, 2e-5, 2000)
+
+
+def batch_machs(seed: int = 4, n: int = 8):
+    """Seeded Mach numbers of the concurrent 128^3 copies, uniform in [1.5, 6]."""
+    return np.random.default_rng(seed).uniform(1.5, 6.0, size=n)
+
+
+def noise(shape, seed: int, amplitude: float = 1.0) -> np.ndarray:
+    """Seeded uniform noise in [-amplitude, amplitude]."""
+    return np.random.default_rng(seed).uniform(-amplitude, amplitude, size=shape)
+
+
+def smooth_random_fields(nx, ny, nz, seed: int, rho0=1.0, u0=(0.3, -0.2, 0.1), T0=1.0, amp=0.1):
+    """Smooth periodic random (rho, u, T): a few seeded Fourier modes on top of a
+    uniform state, small enough to keep rho and T positive."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx, indexing="ij")
+
+    def field():
+        out = np.zeros((nz, ny, nx))
+        for _ in range(3):
+            kx, ky, kz = rng.integers(0, 3, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            out += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * x + ky * y + kz * z) + ph)
+        return out / 3.0
+
+    rho = rho0 * (1.0 + amp * field())
+    u = np.stack([u0[a] + amp * field() for a in range(3)])
+    T = T0 * (1.0 + amp * field())
+    return rho, u, T
