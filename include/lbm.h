@@ -1,0 +1,186 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) D3V15 finite-difference lattice
+ * Boltzmann solver for the 3D compressible Euler equations of Chen, Xu,
+ * Zhang & Li, "Three-Dimensional Lattice Boltzmann Model for High-Speed
+ * Compressible Flows" (arXiv:1010.4135).
+ *
+ * One time step (lbm_step) is the paper's update of the 15 distribution
+ * functions f_i (Sec. 2 velocity set and equilibrium, Sec. 3 NND convection,
+ * extra dissipation term, BGK relaxation, forward Euler) with the boundary
+ * layers of Sec. 4(2).  All arithmetic of the step runs in CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Velocity index i = 0..14 is the paper's i = 1..15: 0 rest; 1..6 = c1
+ *     along +x,-x,+y,-y,+z,-z; 7..14 = c2/sqrt(3) (sx,sy,sz) with the sign
+ *     triples in the order +++,++-,+-+,+--,-++,-+-,--+,---.
+ *   - Dense field arrays are x-fastest over interior cells only:
+ *     rho[z][y][x], T[z][y][x], u[3][z][y][x], f[15][z][y][x].
+ *   - Macroscopic tuples are (rho, u1, u2, u3, T) with R = 1 (p = rho T).
+ *   - Pointers flagged on_device = 1 are device pointers on the device that
+ *     owns the sim; on_device = 0 means ordinary (pageable or pinned) host
+ *     memory, and the call then returns only after the copy has completed.
+ *   - Every call returns an lbm_status (0 = success).  Kernel launches are
+ *     asynchronous on the sim's stream; a fault inside a kernel is reported
+ *     by the next call that synchronises (lbm_sync, lbm_moments, lbm_get_f,
+ *     lbm_conserved, lbm_health, host-pointer lbm_init/lbm_set_f).  A CUDA
+ *     error is sticky: every later call on that sim returns LBM_ESTATE.
+ *   - No kernel traps or spins without bound.
+ *
+ * Ownership: the caller allocates the device workspace (lbm_workspace_bytes)
+ * and the CUDA stream; both must outlive the sim.  The sim owns only a small
+ * host-side descriptor.  The library allocates no device memory.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,      /* invalid argument (sizes, constants, boundary kinds, pointers) */
+  LBM_ENOMEM = -2,      /* workspace smaller than lbm_workspace_bytes() */
+  LBM_ECUDA = -3,       /* a CUDA call failed; the sim is then in LBM_ESTATE */
+  LBM_ENONFINITE = -4,  /* the health flag saw rho <= 0, T <= 0 or a non-finite value */
+  LBM_ETIMEOUT = -5,    /* a bounded device wait ran out */
+  LBM_ESTATE = -6       /* the sim failed earlier; only lbm_destroy is meaningful */
+} lbm_status;
+
+/* Boundary kinds of the two node layers outside a face (Sec. 4(2)). */
+enum {
+  LBM_BC_PERIODIC = 0,    /* wrap; both faces of the axis must be periodic */
+  LBM_BC_FIXED = 1,       /* both layers hold the given (rho,u1,u2,u3,T) */
+  LBM_BC_EXTRAPOLATE = 2, /* g1 = 2 m0 - m1, g2 = 2 g1 - m0 on rho, u, T (needs >= 2 cells) */
+  LBM_BC_REFLECT = 3      /* wall layer: (rho,T,u_t) of the last cell, u_n = 0;
+                             outer layer: the last cell with u_n negated */
+};
+
+/* Storage and arithmetic precision of f. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+
+/* Convection scheme: the paper's NND (Sec. 3), the second-order upwind scheme
+ * of the original Kataoka-Tsutahara model it is compared with (Sec. 3, Fig. 6),
+ * and first-order upwind (the linearisation alpha~ = beta~ = 0 of Sec. 3). */
+enum { LBM_SCHEME_NND = 0, LBM_SCHEME_UPWIND2 = 1, LBM_SCHEME_UPWIND1 = 2 };
+
+/* Health flag bits (lbm_health). */
+enum { LBM_HEALTH_NONFINITE = 1u, LBM_HEALTH_RHO = 2u, LBM_HEALTH_T = 4u, LBM_HEALTH_TIMEOUT = 8u };
+
+/* Step kernel variants of the FP32 path (lbm_set_launch). */
+enum { LBM_VARIANT_TILED = 0, LBM_VARIANT_PLAIN = 1 };
+
+/* Grid of nx*ny*nz interior cells of edge dx and the boundary kind of each
+ * face; fixed_lo/fixed_hi give (rho,u1,u2,u3,T) for FIXED faces (axis 0=x). */
+typedef struct lbm_grid {
+  int32_t nx, ny, nz;
+  int32_t bc_lo[3], bc_hi[3];
+  double fixed_lo[3][5], fixed_hi[3][5];
+} lbm_grid;
+
+/* The discrete-velocity constants c1 != c2, eta0 > 0 (Sec. 2) and the
+ * specific-heat ratio gamma > 1 (b = 2/(gamma-1), Eq. 2). */
+typedef struct lbm_vset {
+  double c1, c2, eta0, gamma;
+} lbm_vset;
+
+typedef struct lbm_sim lbm_sim;
+
+/* Bytes of device workspace a sim of this grid and precision needs (two
+ * padded f buffers, reduction scratch and status words), 0 if the grid is
+ * invalid.  Lets a caller admit work by HBM footprint before allocating. */
+LBM_API size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t precision);
+
+/* Create a sim on the current CUDA device.  tau is the BGK relaxation time
+ * (Eq. 1), dt the time step, dx = dy = dz the cell edge.  d_workspace must be
+ * a device allocation of at least lbm_workspace_bytes() bytes, 256-byte
+ * aligned; cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * The f state is undefined until lbm_init or lbm_set_f.  Errors: LBM_EINVAL
+ * (sizes < 1, c1 == c2, eta0 <= 0, tau/dt/dx <= 0, gamma <= 1, unpaired
+ * periodic faces, EXTRAPOLATE with fewer than 2 cells, NULL pointers),
+ * LBM_ENOMEM (workspace too small), LBM_ECUDA. */
+LBM_API int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt, double dx,
+               int32_t precision, void* d_workspace, size_t ws_bytes, void* cuda_stream, lbm_sim** out);
+
+/* Select the convection scheme (LBM_SCHEME_*) and switch the extra
+ * dissipation term lambda_i Laplacian(f_i) (Eq. "lp") on (1, default) or off (0). */
+LBM_API int lbm_set_scheme(lbm_sim* sim, int32_t scheme, int32_t dissipation);
+
+/* Launch configuration of the FP32 step kernel (the autotuner's knobs):
+ * variant LBM_VARIANT_TILED (default: TMA-staged plane tiles marching in z)
+ * or LBM_VARIANT_PLAIN (one thread per cell, global loads); zchunk = z planes
+ * per CTA of the tiled kernel, 0 = automatic.  Both variants compute the same
+ * update; FP64 sims always use the plain kernel. */
+LBM_API int lbm_set_launch(lbm_sim* sim, int32_t variant, int32_t zchunk);
+
+/* f = f^eq(rho, u, T) at every interior cell (Eq. "eq").  Resets the step
+ * counter and the health flags.  rho, T > 0 is not checked here; the first
+ * step's health flag reports it. */
+LBM_API int lbm_init(lbm_sim* sim, const double* rho, const double* u, const double* T, int32_t on_device);
+
+/* Advance n >= 0 time steps: per step one boundary-fill kernel and one fused
+ * step kernel on the sim's stream; returns without waiting. */
+LBM_API int lbm_step(lbm_sim* sim, int64_t n);
+
+/* (rho, u, T) of every interior cell in double precision (relations e1-e3,
+ * T = (E/rho - u^2)/b).  Synchronises the stream. */
+LBM_API int lbm_moments(lbm_sim* sim, double* rho, double* u, double* T, int32_t on_device);
+
+/* Copy the interior f out / in, dense [15][nz][ny][nx], in the sim's storage
+ * precision (double for LBM_FP64, float for LBM_FP32). */
+LBM_API int lbm_get_f(lbm_sim* sim, void* f, int32_t on_device);
+LBM_API int lbm_set_f(lbm_sim* sim, const void* f, int32_t on_device);
+
+/* Global (mass, momentum x/y/z, energy) summed over interior cells in double
+ * precision by a deterministic reduction (the invariants of relations e1-e3);
+ * out is a host array of 5.  Synchronises; returns LBM_ENONFINITE if the
+ * health flag is set (out is still written). */
+LBM_API int lbm_conserved(lbm_sim* sim, double out[5]);
+
+/* Synchronise and read the health flag bits (LBM_HEALTH_*) accumulated since
+ * lbm_init; returns LBM_ETIMEOUT when a bounded device wait ran out
+ * (LBM_HEALTH_TIMEOUT), else LBM_ENONFINITE when any other bit is set. */
+LBM_API int lbm_health(lbm_sim* sim, uint32_t* flags);
+
+/* Wait for the sim's stream; reports asynchronous kernel faults. */
+LBM_API int lbm_sync(lbm_sim* sim);
+
+/* Steps taken since lbm_init / lbm_set_f. */
+LBM_API int64_t lbm_steps_done(const lbm_sim* sim);
+
+/* Kernel classes of the launch and time accounting below. */
+enum { LBM_KERNEL_FILL = 0, LBM_KERNEL_STEP = 1, LBM_KERNEL_REDUCE = 2, LBM_KERNEL_OTHER = 3, LBM_NKERNEL = 4 };
+
+/* Device-time accounting of this sim's kernels: with enable = 1 every launch
+ * is bracketed by a pair of CUDA events on the sim's stream (a ring of event
+ * pairs, drained as it fills); enable = 0 stops recording.  Launch counts are
+ * kept whether or not timing is on.  Creating the events is the only
+ * allocation this makes (host-side CUDA event objects). */
+LBM_API int lbm_set_timing(lbm_sim* sim, int32_t enable);
+
+/* Synchronise, then report per kernel class (LBM_KERNEL_*) the summed device
+ * milliseconds of timed launches and the number of launches since creation
+ * or the last reset (reset = 1 clears both after reading).  ms and launches
+ * are host arrays of LBM_NKERNEL entries; either may be NULL. */
+LBM_API int lbm_get_timing(lbm_sim* sim, double* ms, int64_t* launches, int32_t reset);
+
+/* Human-readable name of a status code (static string). */
+LBM_API const char* lbm_status_str(int status);
+
+/* Release the descriptor (not the caller's workspace or stream). NULL is ignored. */
+LBM_API void lbm_destroy(lbm_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -324,6 +324,7 @@ static double* pref(padded* P, int i, int x, int y, int z) {
 static void build_padded(const oracle_cfg* c, padded* P, const double* f) {
   const int n[3] = {c->nx, c->ny, c->nz};
   const view I = interior_view(c, f);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int i = 0; i < NV; ++i)
     for (int z = 0; z < n[2]; ++z)
       for (int y = 0; y < n[1]; ++y)
@@ -357,7 +358,7 @@ static void step_padded(const oracle_cfg* c, const padded* P, double* fout, int 
   const int n[3] = {c->nx, c->ny, c->nz};
   const size_t nxy = (size_t)n[0] * n[1], ncell = nxy * n[2];
   (void)nthreads;
-#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
   for (int z = 0; z < n[2]; ++z) {
     for (int y = 0; y < n[1]; ++y) {
       for (int x = 0; x < n[0]; ++x) {
@@ -399,10 +400,14 @@ int oracle_step(const oracle_cfg* c, const double* fin, double* fout, int nthrea
  * the boundary layers on the fly: out[k][15] is the new state of node k. */
 int oracle_step_nodes(const oracle_cfg* c, const double* f, int64_t ncells, const int32_t* xyz, double* out) {
   if (!cfg_valid(c)) return -1;
-  const view I = interior_view(c, f);
   for (int64_t k = 0; k < ncells; ++k) {
     const int x = xyz[3 * k], y = xyz[3 * k + 1], z = xyz[3 * k + 2];
     if (x < 0 || y < 0 || z < 0 || x >= c->nx || y >= c->ny || z >= c->nz) return -1;
+  }
+  const view I = interior_view(c, f);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t k = 0; k < ncells; ++k) {
+    const int x = xyz[3 * k], y = xyz[3 * k + 1], z = xyz[3 * k + 2];
     double S[NV][3][5];
     for (int i = 0; i < NV; ++i)
       for (int a = 0; a < 3; ++a)
@@ -430,8 +435,9 @@ int oracle_padded(const oracle_cfg* c, const double* f, double* out) {
 
 /* f = f^eq(rho, u, T) at every interior node. */
 void oracle_init(const oracle_cfg* c, const double* rho, const double* u, const double* T, double* f) {
-  const size_t ncell = (size_t)c->nx * c->ny * c->nz;
-  for (size_t k = 0; k < ncell; ++k) {
+  const int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < ncell; ++k) {
     double uu[3] = {u[k], u[ncell + k], u[2 * ncell + k]}, feq[NV];
     oracle_feq(c, rho[k], uu, T[k], feq);
     for (int i = 0; i < NV; ++i) f[i * ncell + k] = feq[i];
@@ -440,8 +446,9 @@ void oracle_init(const oracle_cfg* c, const double* rho, const double* u, const 
 
 /* Macroscopic fields of every interior node. */
 void oracle_macros(const oracle_cfg* c, const double* f, double* rho, double* u, double* T) {
-  const size_t ncell = (size_t)c->nx * c->ny * c->nz;
-  for (size_t k = 0; k < ncell; ++k) {
+  const int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < ncell; ++k) {
     double fc[NV], out[6];
     for (int i = 0; i < NV; ++i) fc[i] = f[i * ncell + k];
     oracle_moments(c, fc, out);
