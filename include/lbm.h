@@ -146,6 +146,23 @@ LBM_API int lbm_set_f(lbm_sim* sim, const void* f, int32_t on_device);
  * health flag is set (out is still written). */
 LBM_API int lbm_conserved(lbm_sim* sim, double out[5]);
 
+/* Global (mass, momentum x/y/z, energy) of a dense device array
+ * f[15][nz][ny][nx] (the layout lbm_get_f writes, float or double per
+ * precision) for callers that cannot allocate device memory: code running
+ * while a stream is captured into a CUDA graph, hosts whose allocator owns all
+ * of device memory, and monitoring hooks that must not change the device's
+ * memory footprint.  The paper has no counterpart; this is a deployment
+ * convenience.  No workspace and no allocation: the per-block partial sums
+ * live in one static 256 KiB device array that every GPU loading this library
+ * keeps until exit.  At most 33,554,432 cells (4096 blocks of 8192 cells);
+ * larger grids return LBM_EINVAL.  The first call on a device looks up the
+ * array's address, so make it before any stream capture.  All calls share the
+ * array: calls that overlap on the same GPU race and give wrong sums.  out is
+ * 5 doubles, in device memory (out_on_device = 1; asynchronous on
+ * cuda_stream) or host memory (the call synchronises cuda_stream). */
+LBM_API int lbm_conserved_noalloc(const void* f, int32_t precision, int32_t nx, int32_t ny, int32_t nz,
+                                  const lbm_vset* vset, double* out, int32_t out_on_device, void* cuda_stream);
+
 /* Synchronise and read the health flag bits (LBM_HEALTH_*) accumulated since
  * lbm_init; returns LBM_ETIMEOUT when a bounded device wait ran out
  * (LBM_HEALTH_TIMEOUT), else LBM_ENONFINITE when any other bit is set. */

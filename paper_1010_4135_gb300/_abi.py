@@ -51,6 +51,8 @@ SIGNATURES = [
     ("lbm_get_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     ("lbm_set_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     ("lbm_conserved", ctypes.c_int, [_vp, _dp]),
+    ("lbm_conserved_noalloc", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(lbm_vset), _vp, ctypes.c_int32, _vp]),
     ("lbm_health", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     ("lbm_sync", ctypes.c_int, [_vp]),
     ("lbm_steps_done", ctypes.c_int64, [_vp]),
@@ -110,6 +112,7 @@ lbm_moments = _forward("lbm_moments")
 lbm_get_f = _forward("lbm_get_f")
 lbm_set_f = _forward("lbm_set_f")
 lbm_conserved = _forward("lbm_conserved")
+lbm_conserved_noalloc = _forward("lbm_conserved_noalloc")
 lbm_health = _forward("lbm_health")
 lbm_sync = _forward("lbm_sync")
 lbm_steps_done = _forward("lbm_steps_done")
