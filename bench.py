@@ -38,9 +38,16 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    p.add_argument("--workload", default="droplet", choices=["droplet", "bubble"])
+    p.add_argument("--requests", type=int, default=200, help="serve: number of requests in the trace")
+    p.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
+    p.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serve: workspace budget (0 = 80%% of free)")
+    p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "serve"],
+                   help="droplet: 256^3 Mach-2 shock-droplet; bubble: 512x256x256 Mach-3 shock-bubble; "
+                        "batch: the bubble grid plus 8 128^3 copies with seeded Mach numbers, one launch per "
+                        "step, replayed as a CUDA graph; serve: the seeded request stream through the "
+                        "continuous-batching server")
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
-    p.add_argument("--variant", default="tiled", choices=["tiled", "plain"], help="FP32 step kernel")
+    p.add_argument("--variant", default="tiled", choices=["tiled", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
     p.add_argument("--zchunk", type=int, default=0, help="z planes per CTA of the tiled kernel (0 = auto)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -49,7 +56,85 @@ def parse():
 
 def workload(name):
     import workloads
-    return workloads.shock_droplet(256) if name == "droplet" else workloads.shock_bubble()
+    if name == "droplet":
+        return workloads.shock_droplet(256)
+    return workloads.shock_bubble()
+
+
+def batch_workloads():
+    """The 512x256x256 Mach-3 bubble and 8 128^3 bubbles whose Mach numbers
+    are drawn (seed 4) uniformly in [1.5, 6]; (c1, c2, eta0, dt) of each from
+    the von Neumann parameter rule (paper_1010_4135_gb300.stability) applied
+    to the initial states and to the star states of the shock meeting the
+    bubble."""
+    import workloads
+    from paper_1010_4135_gb300 import stability
+    out = []
+    for n, mach in [((512, 256, 256), 3.0)] + [((128, 128, 128), float(m)) for m in workloads.batch_machs(4, 8)]:
+        r2, u2, p2, _ = workloads.rankine_hugoniot(mach)
+        post, bubble = (r2, u2, 0.0, 0.0, p2 / r2), (0.1, 0.0, 0.0, 0.0, 10.0)
+        states = [(1.0, 0.0, 0.0, 0.0, 1.0), post, bubble, *stability.interaction_states(post, bubble)]
+        c1, c2, eta0, dt = stability.choose_parameters(states, 1.0 / n[1])
+        w = workloads.shock_bubble(*n, mach=mach, c=(c1, c2, eta0), dt=dt)
+        w.name = f"shock_bubble_{n[0]}x{n[1]}x{n[2]}_mach{mach:.2f}"
+        out.append(w)
+    return out
+
+
+def run_batch(args):
+    """One step = one batched launch advancing all nine grids; the timed steps
+    replay a captured CUDA graph of `graph_steps` steps."""
+    import torch
+    from paper_1010_4135_gb300 import sim as S
+    torch.cuda.set_device(0)
+    ws = batch_workloads()
+    sims = []
+    for w in ws:
+        s = S.from_workload(w, precision="fp32")
+        rho, u, T = w.initial_fields()
+        s.init(rho, u, T)
+        sims.append(s)
+    cells = sum(w.ncell for w in ws)
+    S.step_batch(sims, max(2, args.warmup))
+    gsteps = 10 if args.steps % 10 == 0 else 2
+    steps = max(gsteps, args.steps - args.steps % gsteps)
+    g = S.Graph(sims, gsteps)
+    g.launch(1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_smi_id(torch, 0))
+    time.sleep(0.5)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ev0.record(sims[0].stream)
+    g.launch(steps // gsteps)
+    ev1.record(sims[0].stream)
+    ev1.synchronize()
+    t1 = time.time()
+    ms = ev0.elapsed_time(ev1)
+    clock = clocks.summary(t0, t1)
+    clocks.stop()
+    health = [s.health() for s in sims]
+    peak, peak_kind = measured_peak()
+    alg = 120.0 * cells
+    per_step = ms * 1e-3 / steps
+    line = {
+        "metric": METRIC, "value": cells * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch: " + ", ".join(w.name for w in ws), "cells": cells,
+                   "c1_c2_eta0_dt": [[w.c1, w.c2, w.eta0, w.dt] for w in ws],
+                   "launch": f"one persistent batched step kernel per step, CUDA graph of {gsteps} steps",
+                   "l2": "no flush: 18 f buffers of 1.0-2.0 GB / 0.13 GB exceed the L2"},
+        "roofline": {"bound": "hbm", "achieved": alg / per_step / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / per_step / 1e9 / peak, "peak_source": peak_kind,
+                     "kernel": "step_pair_batch (all grids, one launch per step; time per step incl. graph gaps)",
+                     "traffic": None},
+        "gpu_launches": steps, "clocks": clock, "health_flags": health,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def describe(w, precision):
@@ -226,14 +311,11 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
+    from paper_1010_4135_gb300 import replicas
+    rank, world, local = replicas.env_ranks()
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        replicas.init("nccl", device=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
@@ -247,8 +329,7 @@ def run_ours(args):
 
     def barrier():
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     s.step(args.warmup)
@@ -271,15 +352,10 @@ def run_ours(args):
     per_kernel = s.timing(reset=True)
     s.set_timing(False)
     health = s.health()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max, total_cells = replicas.aggregate(ms, w.ncell * args.steps, device=torch.device("cuda", dev))
     clock = clocks.summary(t0, t1) if clocks else None
     if clocks:
         clocks.stop()
-    total_cells = w.ncell * args.steps * world
     value = total_cells / (ms_max * 1e-3)
 
     # conservation sums of the final state (FP64, deterministic reduction)
@@ -305,18 +381,14 @@ def run_ours(args):
         A.check(A.lbm_moments(s.handle, ctypes.c_void_p(orho.data_ptr()), ctypes.c_void_p(ou.data_ptr()),
                               ctypes.c_void_p(oT.data_ptr()), 0), "lbm_moments")
         te = time.perf_counter() - t0e
-        if dist is not None:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te, _ = replicas.aggregate(te, 0, device=torch.device("cuda", dev))
         io = (hr.numel() + hu.numel() + hT.numel()) * 8
         e2e = {"value": total_cells / te, "unit": UNIT,
                "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
                "note": "per run: lbm_init from pinned host (rho,u,T) + steps + lbm_moments to pinned host"}
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        replicas.finish()
         return 0
 
     step_ms, step_n = per_kernel["step"]
@@ -353,8 +425,50 @@ def run_ours(args):
         "conserved_final": cons,
     }
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    replicas.finish()
+    return 0
+
+
+def run_serve(args):
+    """The seeded Poisson request stream served in real time; reports latency
+    percentiles, throughput and the L1 density error of sampled requests
+    against the FP64 path (parity-checked against the oracle)."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1010_4135_gb300 import serve
+    from paper_1010_4135_gb300 import sim as S
+    torch.cuda.set_device(0)
+    trace = workloads.serving_trace(seed=5, n=args.requests, rate=args.rate)
+    budget = int(args.hbm_budget_gb * 2 ** 30) if args.hbm_budget_gb > 0 else None
+    srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True)
+    done = srv.run(trace)
+    stats = serve.summary(done, srv.wall)
+    # L1(rho) of the three smallest finished requests against the FP64 path
+    sample = sorted(done, key=lambda j: (int(np.prod(j.req["grid"])) * j.req["steps"], j.req["id"]))[:3]
+    l1 = []
+    for j in sample:
+        w = workloads.request_workload(j.req, *j.params)
+        s = S.from_workload(w, precision="fp64")
+        rho, u, T = w.initial_fields()
+        s.init(rho, u, T)
+        s.step(j.req["steps"])
+        r64, _, _ = s.moments()
+        s.close()
+        l1.append({"id": j.req["id"], "grid": list(j.req["grid"]), "steps": j.req["steps"], "mach": j.req["mach"],
+                   "l1_rho": float(np.abs(j.rho - r64).sum() / np.abs(r64).sum())})
+    line = {
+        "metric": METRIC, "value": stats["cell_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": int(sum(j.req["steps"] for j in done)), "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {args.requests} requests, Poisson rate {args.rate}/s (seed 5), grids "
+                               "64^3..256^3, Mach U[1.2,10], density ratio log-U[0.1,10], 500-3000 steps, FP32",
+                   "hbm_budget_bytes": srv.budget, "peak_resident_bytes": srv.peak_bytes,
+                   "peak_batch": srv.peak_batch},
+        "serving": stats, "l1_vs_fp64_sample": l1, "gpu_launches": srv.launches,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -362,6 +476,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

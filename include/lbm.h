@@ -76,8 +76,15 @@ enum { LBM_SCHEME_NND = 0, LBM_SCHEME_UPWIND2 = 1, LBM_SCHEME_UPWIND1 = 2 };
 /* Health flag bits (lbm_health). */
 enum { LBM_HEALTH_NONFINITE = 1u, LBM_HEALTH_RHO = 2u, LBM_HEALTH_T = 4u, LBM_HEALTH_TIMEOUT = 8u };
 
-/* Step kernel variants of the FP32 path (lbm_set_launch). */
-enum { LBM_VARIANT_TILED = 0, LBM_VARIANT_PLAIN = 1 };
+/* Step kernel variants of the FP32 path (lbm_set_launch): TILED = TMA plane
+ * tiles of 32 x 8 cells, two x-adjacent cells per thread in packed f32x2
+ * arithmetic (default); the step kernel also writes the periodic images and
+ * the extrapolated / reflected x-face layers of the state it produces, so no
+ * fill launch is needed between steps; TILED_FILL = the same kernel with all
+ * boundary layers left to a fill launch before each step; TILED_SINGLE = the
+ * same tiles, one cell per thread; PLAIN = one thread per cell reading
+ * global memory. */
+enum { LBM_VARIANT_TILED = 0, LBM_VARIANT_PLAIN = 1, LBM_VARIANT_TILED_SINGLE = 2, LBM_VARIANT_TILED_FILL = 3 };
 
 /* Grid of nx*ny*nz interior cells of edge dx and the boundary kind of each
  * face; fixed_lo/fixed_hi give (rho,u1,u2,u3,T) for FIXED faces (axis 0=x). */
@@ -116,11 +123,17 @@ LBM_API int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, d
 LBM_API int lbm_set_scheme(lbm_sim* sim, int32_t scheme, int32_t dissipation);
 
 /* Launch configuration of the FP32 step kernel (the autotuner's knobs):
- * variant LBM_VARIANT_TILED (default: TMA-staged plane tiles marching in z)
- * or LBM_VARIANT_PLAIN (one thread per cell, global loads); zchunk = z planes
- * per CTA of the tiled kernel, 0 = automatic.  Both variants compute the same
- * update; FP64 sims always use the plain kernel. */
+ * a LBM_VARIANT_* value; zchunk = z planes per CTA of the tiled kernels,
+ * 0 = automatic.  All variants compute the same update (to float rounding);
+ * FP64 sims always use the plain kernel. */
 LBM_API int lbm_set_launch(lbm_sim* sim, int32_t variant, int32_t zchunk);
+
+/* Polls the tiled step kernels make on a shared-memory copy barrier before
+ * giving up (default 2^22, seconds of waiting).  On giving up a kernel sets
+ * LBM_HEALTH_TIMEOUT, lets its copies in flight finish (with the default
+ * limit) and returns; lbm_health then reports LBM_ETIMEOUT and the device
+ * stays usable.  A small value exercises that path (0 gives up at once). */
+LBM_API int lbm_set_wait_limit(lbm_sim* sim, uint32_t polls);
 
 /* f = f^eq(rho, u, T) at every interior cell (Eq. "eq").  Resets the step
  * counter and the health flags.  rho, T > 0 is not checked here; the first
@@ -173,6 +186,31 @@ LBM_API int lbm_sync(lbm_sim* sim);
 
 /* Steps taken since lbm_init / lbm_set_f. */
 LBM_API int64_t lbm_steps_done(const lbm_sim* sim);
+
+/* Most grids one batched step can carry. */
+#define LBM_MAX_BATCH 48
+
+/* Advance n sims by `steps` time steps together.  Per step, one launch of the
+ * persistent FP32 tile kernel walks a descriptor table holding every grid's
+ * tiles (uneven grids, different constants and boundaries are fine), plus a
+ * fill launch only for boundary layers that kernel does not write itself.
+ * All sims must be FP32 with the default tiled variant and the same scheme,
+ * live on the current device and share one stream (sims[0]'s); 1 <= n <=
+ * LBM_MAX_BATCH.  Each sim's result is bitwise the one lbm_step gives it
+ * alone.  Returns without waiting; LBM_EINVAL on a mismatch. */
+LBM_API int lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t steps);
+
+/* A CUDA graph of `steps` (even, >= 2) time steps of one sim (n = 1, any
+ * precision or variant) or of a batch (the lbm_step_batch rules).  Capture
+ * launches nothing; each lbm_graph_launch replays all the steps with one
+ * graph launch on the sims' stream and advances their step counters.  A
+ * replay is refused (LBM_ESTATE) if a sim was stepped an odd number of times
+ * outside the graph since the capture (its buffers would be swapped).
+ * Graph instantiation allocates driver resources; destroy releases them. */
+typedef struct lbm_graph lbm_graph;
+LBM_API int lbm_graph_capture(lbm_sim* const* sims, int32_t n, int64_t steps, lbm_graph** out);
+LBM_API int lbm_graph_launch(lbm_graph* graph);
+LBM_API void lbm_graph_destroy(lbm_graph* graph);
 
 /* Kernel classes of the launch and time accounting below. */
 enum { LBM_KERNEL_FILL = 0, LBM_KERNEL_STEP = 1, LBM_KERNEL_REDUCE = 2, LBM_KERNEL_OTHER = 3, LBM_NKERNEL = 4 };

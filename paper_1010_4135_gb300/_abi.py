@@ -16,9 +16,10 @@ LBM_BC_PERIODIC, LBM_BC_FIXED, LBM_BC_EXTRAPOLATE, LBM_BC_REFLECT = 0, 1, 2, 3
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_SCHEME_NND, LBM_SCHEME_UPWIND2, LBM_SCHEME_UPWIND1 = 0, 1, 2
 LBM_HEALTH_NONFINITE, LBM_HEALTH_RHO, LBM_HEALTH_T, LBM_HEALTH_TIMEOUT = 1, 2, 4, 8
-LBM_VARIANT_TILED, LBM_VARIANT_PLAIN = 0, 1
+LBM_VARIANT_TILED, LBM_VARIANT_PLAIN, LBM_VARIANT_TILED_SINGLE, LBM_VARIANT_TILED_FILL = 0, 1, 2, 3
 LBM_KERNEL_FILL, LBM_KERNEL_STEP, LBM_KERNEL_REDUCE, LBM_KERNEL_OTHER, LBM_NKERNEL = 0, 1, 2, 3, 4
 KERNEL_NAMES = ("fill", "step", "reduce", "other")
+LBM_MAX_BATCH = 48
 
 
 class lbm_grid(ctypes.Structure):
@@ -45,8 +46,13 @@ SIGNATURES = [
                                   ctypes.POINTER(_vp)]),
     ("lbm_set_scheme", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("lbm_set_launch", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("lbm_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint32]),
     ("lbm_init", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
     ("lbm_step", ctypes.c_int, [_vp, ctypes.c_int64]),
+    ("lbm_step_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int64]),
+    ("lbm_graph_capture", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(_vp)]),
+    ("lbm_graph_launch", ctypes.c_int, [_vp]),
+    ("lbm_graph_destroy", None, [_vp]),
     ("lbm_moments", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
     ("lbm_get_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     ("lbm_set_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
@@ -106,8 +112,13 @@ lbm_workspace_bytes = _forward("lbm_workspace_bytes")
 lbm_create = _forward("lbm_create")
 lbm_set_scheme = _forward("lbm_set_scheme")
 lbm_set_launch = _forward("lbm_set_launch")
+lbm_set_wait_limit = _forward("lbm_set_wait_limit")
 lbm_init = _forward("lbm_init")
 lbm_step = _forward("lbm_step")
+lbm_step_batch = _forward("lbm_step_batch")
+lbm_graph_capture = _forward("lbm_graph_capture")
+lbm_graph_launch = _forward("lbm_graph_launch")
+lbm_graph_destroy = _forward("lbm_graph_destroy")
 lbm_moments = _forward("lbm_moments")
 lbm_get_f = _forward("lbm_get_f")
 lbm_set_f = _forward("lbm_set_f")

@@ -1,6 +1,7 @@
 // Boundary fill, initialisation, moments, pack/unpack and the FP64
-// conservation reduction.  All of these work in double precision whatever
-// the storage type of f.
+// conservation reduction.  Initialisation and moments compute in double
+// precision whatever the storage type of f; the boundary fill computes in the
+// storage precision (its results are stored at that precision).
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -24,69 +25,94 @@ __device__ __forceinline__ void macros_at(const Model<double>& m, const double v
   out[0] = rho; out[1] = ux; out[2] = uy; out[3] = uz; out[4] = T;
 }
 
+// Error-free sum of two floats: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Running sum of floats held as an unevaluated pair hi + lo (about 44
+// significant bits).  add() is exact up to the rounding of lo, which stays
+// of order 2^-24 |hi|, so n additions lose about n * 2^-48 relative.
+struct DFloat {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    lo += e;
+    two_sum(s, lo, hi, lo);  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // One thread per (face position): writes the two node layers outside a face.
-// blockIdx.y = face (2*axis + hi).  Sec. 4(2) boundary rules, ghost f = f^eq.
-template <typename R>
-__global__ void fill_kernel(R* __restrict__ f, Layout L, Model<double> m, BcDesc bc) {
+// blockIdx.y = face (2*axis + hi); faces whose bit is clear in `mask` are
+// skipped.  Sec. 4(2) boundary rules, ghost f = f^eq.  M is the arithmetic
+// type (the storage type of f: ghost values are stored at that precision).
+template <typename R, typename M>
+__global__ void fill_kernel(R* __restrict__ f, Layout L, Model<M> m, BcDesc bc, unsigned mask) {
   const int face = blockIdx.y;
+  if (!((mask >> face) & 1u)) return;
   const int axis = face >> 1, hi = face & 1;
-  const int n[3] = {L.nx, L.ny, L.nz};
-  const int a1 = axis == 0 ? 1 : 0;
-  const int a2 = axis == 2 ? 1 : 2;
+  // cross-section coordinates (s1 fastest) and the element stride along the face normal
+  const int n1 = axis == 0 ? L.ny : L.nx;
+  const int n2 = axis == 2 ? L.ny : L.nz;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long count = (long long)n[a1] * n[a2];
-  if (p >= count) return;
-  int q[3];
-  q[a1] = (int)(p % n[a1]);
-  q[a2] = (int)(p / n[a1]);
-  const int N = n[axis];
+  if (p >= (long long)n1 * n2) return;
+  const int s1 = (int)(p % n1), s2 = (int)(p / n1);
+  const long long base = axis == 0 ? L.at(0, s1, s2) : (axis == 1 ? L.at(s1, 0, s2) : L.at(s1, s2, 0));
+  const long long step = axis == 0 ? 1LL : (axis == 1 ? (long long)L.sx : L.plane);
+  const int N = axis == 0 ? L.nx : (axis == 1 ? L.ny : L.nz);
   const int kind = bc.kind[face];
   const int g1 = hi ? N : -1, g2 = hi ? N + 1 : -2;
-  auto index = [&](int k) {
-    int c[3] = {q[0], q[1], q[2]};
-    c[axis] = k;
-    return L.at(c[0], c[1], c[2]);
-  };
+  const long long i1 = base + g1 * step, i2 = base + g2 * step;
   if (kind == LBM_BC_PERIODIC) {
-    const int s1 = ((g1 % N) + N) % N, s2 = ((g2 % N) + N) % N;
-    const long long d1 = index(g1), d2 = index(g2), r1 = index(s1), r2 = index(s2);
+    const long long r1 = base + (((g1 % N) + N) % N) * step, r2 = base + (((g2 % N) + N) % N) * step;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       const R v1 = f[i * L.fs + r1], v2 = f[i * L.fs + r2];
-      f[i * L.fs + d1] = v1;
-      f[i * L.fs + d2] = v2;
+      f[i * L.fs + i1] = v1;
+      f[i * L.fs + i2] = v2;
     }
     return;
   }
-  double G1[5], G2[5];
+  M G1[5], G2[5];
   if (kind == LBM_BC_FIXED) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) G1[k] = G2[k] = bc.fixed[face][k];
+    for (int k = 0; k < 5; ++k) G1[k] = G2[k] = (M)bc.fixed[face][k];
   } else {
-    double v[NV], M0[5];
-    load_cell(f, L.fs, index(hi ? N - 1 : 0), v);
-    macros_at(m, v, M0);
+    const long long m0 = base + (hi ? N - 1 : 0) * step;
+    M v[NV], M0[5];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = (M)f[i * L.fs + m0];
+    moments(m, v, M0[0], M0[1], M0[2], M0[3], M0[4]);
     if (kind == LBM_BC_EXTRAPOLATE) {
-      double M1[5];
-      load_cell(f, L.fs, index(hi ? N - 2 : 1), v);
-      macros_at(m, v, M1);
+      const long long m1 = base + (hi ? N - 2 : 1) * step;
+      M M1[5];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = (M)f[i * L.fs + m1];
+      moments(m, v, M1[0], M1[1], M1[2], M1[3], M1[4]);
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        G1[k] = 2.0 * M0[k] - M1[k];
-        G2[k] = 2.0 * G1[k] - M0[k];
+        G1[k] = M(2) * M0[k] - M1[k];
+        G2[k] = M(2) * G1[k] - M0[k];
       }
-    } else {  // LBM_BC_REFLECT
+    } else {  // LBM_BC_REFLECT: the normal velocity is component 1 + axis
 #pragma unroll
       for (int k = 0; k < 5; ++k) G1[k] = G2[k] = M0[k];
-      G1[1 + axis] = 0.0;
-      G2[1 + axis] = -M0[1 + axis];
+      const M un = axis == 0 ? M0[1] : (axis == 1 ? M0[2] : M0[3]);
+      if (axis == 0) { G1[1] = M(0); G2[1] = -un; }
+      if (axis == 1) { G1[2] = M(0); G2[2] = -un; }
+      if (axis == 2) { G1[3] = M(0); G2[3] = -un; }
     }
   }
-  double e[NV];
+  M e[NV];
   equilibrium(m, G1[0], G1[1], G1[2], G1[3], G1[4], e);
-  store_cell(f, L.fs, index(g1), e);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) f[i * L.fs + i1] = (R)e[i];
   equilibrium(m, G2[0], G2[1], G2[2], G2[3], G2[4], e);
-  store_cell(f, L.fs, index(g2), e);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) f[i * L.fs + i2] = (R)e[i];
 }
 
 __device__ __forceinline__ bool cell_of(const Layout& L, long long k, int& x, int& y, int& z) {
@@ -149,49 +175,75 @@ __global__ void unpack_kernel(R* __restrict__ f, Layout L, const R* __restrict__
 
 constexpr int RED_THREADS = 256;
 
-// Deterministic FP64 sums of (rho, rho u, E) over interior cells: a fixed
-// grid-stride assignment, a fixed shared-memory tree per block, and the last
-// block to finish adding the per-block partials in block order.
+__device__ __forceinline__ bool finite_value(double v) { return fabs(v) < 1e300; }
+__device__ __forceinline__ bool finite_value(float v) { return fabsf(v) < 3.0e38f; }
+
+// Per-field accumulation of one thread's cells: double for double storage;
+// for float storage an error-free double-float pair, converted to double at
+// the end (GB300's FP64 rate would make a per-value conversion and double
+// add the bottleneck of this memory-bound reduction).
+template <typename R>
+struct FieldAcc;
+template <>
+struct FieldAcc<double> {
+  double s[NV];
+  __device__ FieldAcc() {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double v) { s[i] += v; }
+  __device__ __forceinline__ double value(int i) const { return s[i]; }
+};
+template <>
+struct FieldAcc<float> {
+  DFloat s[NV];
+  __device__ __forceinline__ void add(int i, float v) { s[i].add(v); }
+  __device__ __forceinline__ double value(int i) const { return s[i].value(); }
+};
+
+// Deterministic FP64 global sums of (rho, rho u, E) over interior cells.  The
+// moments are linear in f, so the kernel sums each field f_i over the cells
+// (a fixed grid-stride assignment, a fixed shared-memory tree per block) and
+// the last block to finish adds the per-block field totals in block order and
+// combines them: mass = sum_i F_i, momentum = sum_i v_i F_i, energy =
+// sum_i (v_i^2 + eta_i^2) F_i.
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restrict__ f, Layout L, Model<double> m,
                                                                 double* __restrict__ partials,
                                                                 unsigned* __restrict__ counter,
                                                                 double* __restrict__ result,
                                                                 unsigned* __restrict__ flags) {
-  __shared__ double sh[5][RED_THREADS];
+  __shared__ double sh[RED_THREADS];
+  __shared__ double tot[NV];
   __shared__ bool last;
-  double acc[5] = {0, 0, 0, 0, 0};
+  FieldAcc<R> acc;
   bool bad = false;
   const long long n = L.ncell();
   for (long long k = (long long)blockIdx.x * RED_THREADS + threadIdx.x; k < n; k += (long long)gridDim.x * RED_THREADS) {
     int x, y, z;
     cell_of(L, k, x, y, z);
-    double v[NV];
-    load_cell(f, L.fs, L.at(x, y, z), v);
-    const double sa = ((v[1] + v[2]) + (v[3] + v[4])) + (v[5] + v[6]);
-    const double sd = ((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14]));
-    const double rho = v[0] + sa + sd;
-    const double mx = m.c1 * (v[1] - v[2]) + m.s * (((v[7] + v[8]) + (v[9] + v[10])) - ((v[11] + v[12]) + (v[13] + v[14])));
-    const double my = m.c1 * (v[3] - v[4]) + m.s * (((v[7] + v[8]) + (v[11] + v[12])) - ((v[9] + v[10]) + (v[13] + v[14])));
-    const double mz = m.c1 * (v[5] - v[6]) + m.s * (((v[7] + v[9]) + (v[11] + v[13])) - ((v[8] + v[10]) + (v[12] + v[14])));
-    const double E = m.eta0sq * v[0] + m.c1sq * sa + m.c2sq * sd;
-    acc[0] += rho; acc[1] += mx; acc[2] += my; acc[3] += mz; acc[4] += E;
-    bad |= !(fabs(rho) + fabs(E) < 1e300);
+    const long long idx = L.at(x, y, z);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      const R v = f[i * L.fs + idx];
+      bad |= !finite_value(v);
+      acc.add(i, v);
+    }
   }
   if (bad) atomicOr(flags, (unsigned)LBM_HEALTH_NONFINITE);
-#pragma unroll
-  for (int j = 0; j < 5; ++j) sh[j][threadIdx.x] = acc[j];
-  __syncthreads();
-  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-#pragma unroll
-      for (int j = 0; j < 5; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+  for (int i = 0; i < NV; ++i) {
+    sh[threadIdx.x] = acc.value(i);
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
     }
+    if (threadIdx.x == 0) tot[i] = sh[0];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) partials[blockIdx.x * 8 + j] = sh[j][0];
+    for (int i = 0; i < NV; ++i) partials[blockIdx.x * 16 + i] = tot[i];
     __threadfence();
     const unsigned done = atomicAdd(counter, 1u);
     last = (done == gridDim.x - 1);
@@ -199,13 +251,20 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    double s[5] = {0, 0, 0, 0, 0};
+    double F[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) F[i] = 0.0;
     for (unsigned b = 0; b < gridDim.x; ++b) {
 #pragma unroll
-      for (int j = 0; j < 5; ++j) s[j] += ((volatile double*)partials)[b * 8 + j];
+      for (int i = 0; i < NV; ++i) F[i] += ((volatile double*)partials)[b * 16 + i];
     }
-#pragma unroll
-    for (int j = 0; j < 5; ++j) result[j] = s[j];
+    const double sa = ((F[1] + F[2]) + (F[3] + F[4])) + (F[5] + F[6]);
+    const double sd = ((F[7] + F[8]) + (F[9] + F[10])) + ((F[11] + F[12]) + (F[13] + F[14]));
+    result[0] = F[0] + sa + sd;
+    result[1] = m.c1 * (F[1] - F[2]) + m.s * (((F[7] + F[8]) + (F[9] + F[10])) - ((F[11] + F[12]) + (F[13] + F[14])));
+    result[2] = m.c1 * (F[3] - F[4]) + m.s * (((F[7] + F[8]) + (F[11] + F[12])) - ((F[9] + F[10]) + (F[13] + F[14])));
+    result[3] = m.c1 * (F[5] - F[6]) + m.s * (((F[7] + F[9]) + (F[11] + F[13])) - ((F[8] + F[10]) + (F[12] + F[14])));
+    result[4] = m.eta0sq * F[0] + m.c1sq * sa + m.c2sq * sd;
     *counter = 0u;
   }
 }
@@ -214,13 +273,16 @@ inline int blocks_for(long long n, int threads) { return (int)((n + threads - 1)
 
 }  // namespace
 
-cudaError_t launch_fill(int prec, void* f, const Layout& L, const Model<double>& m, const BcDesc& bc, cudaStream_t st) {
-  const long long c0 = (long long)L.ny * L.nz, c1 = (long long)L.nx * L.nz, c2 = (long long)L.nx * L.ny;
-  long long cmax = c0 > c1 ? c0 : c1;
-  cmax = cmax > c2 ? cmax : c2;
+cudaError_t launch_fill(int prec, void* f, const Layout& L, const Model<double>& md, const Model<float>& mf,
+                        const BcDesc& bc, unsigned mask, cudaStream_t st) {
+  if (!mask) return cudaSuccess;
+  long long cmax = 1;
+  const long long cnt[3] = {(long long)L.ny * L.nz, (long long)L.nx * L.nz, (long long)L.nx * L.ny};
+  for (int a = 0; a < 3; ++a)
+    if (((mask >> (2 * a)) & 3u) && cnt[a] > cmax) cmax = cnt[a];
   dim3 grid((unsigned)((cmax + 127) / 128), 6);
-  if (prec == LBM_FP64) fill_kernel<double><<<grid, 128, 0, st>>>((double*)f, L, m, bc);
-  else fill_kernel<float><<<grid, 128, 0, st>>>((float*)f, L, m, bc);
+  if (prec == LBM_FP64) fill_kernel<double, double><<<grid, 128, 0, st>>>((double*)f, L, md, bc, mask);
+  else fill_kernel<float, float><<<grid, 128, 0, st>>>((float*)f, L, mf, bc, mask);
   return cudaGetLastError();
 }
 

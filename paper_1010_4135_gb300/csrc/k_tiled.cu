@@ -17,62 +17,12 @@
 // Every wait on an mbarrier is bounded; on timeout the CTA sets
 // LBM_HEALTH_TIMEOUT in the status word, waits (bounded) for its own copies in
 // flight and returns.
-#include <cuda.h>
-
-#include "lbm_internal.cuh"
+#include "tma_ring.cuh"
 
 namespace lbm {
 namespace {
 
-constexpr int TX = 32, TY = 8;
-constexpr int BX = TX + 4, BY = TY + 4;     // tile with a 2-cell halo
-constexpr int PL = BX * BY;                 // floats per field in one plane tile
-constexpr int SLOT_BYTES_TX = NV * PL * 4;  // bytes one TMA copy delivers (25,920)
-constexpr int SLOT_STRIDE = 25984;          // slot pitch: 128-byte multiple >= SLOT_BYTES_TX
-constexpr int NSLOT = 4;
-constexpr int SMEM_BYTES = NSLOT * SLOT_STRIDE + NSLOT * 8;
-constexpr unsigned WAIT_LIMIT = 1u << 22;   // try_wait polls before giving up (seconds)
-
-static_assert(SLOT_STRIDE % 128 == 0 && SLOT_STRIDE >= SLOT_BYTES_TX, "slot pitch");
-static_assert(BX * 4 % 16 == 0, "TMA box inner extent must be a 16-byte multiple");
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-
-// Bounded wait; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* map, int x, int y, int z,
-                                               uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
-      : "memory");
-}
+using namespace ring;
 
 template <int SCHEME>
 __global__ void __launch_bounds__(TX* TY, 2)
@@ -267,13 +217,6 @@ __global__ void __launch_bounds__(TX* TY, 2)
 template <int SCHEME>
 cudaError_t launch_scheme(const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
                           const Model<float>& m, int zc, unsigned* flags, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<SCHEME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   dim3 block(TX, TY, 1);
   dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
   step_tiled_kernel<SCHEME><<<grid, block, SMEM_BYTES, st>>>(map, fin, fout, L, m, zc, flags);
@@ -281,6 +224,18 @@ cudaError_t launch_scheme(const CUtensorMap& map, const float* fin, float* fout,
 }
 
 }  // namespace
+
+cudaError_t prepare_tiled_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<LBM_SCHEME_NND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_tiled_kernel<LBM_SCHEME_UPWIND2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step_tiled_kernel<LBM_SCHEME_UPWIND1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES);
+  return e;
+}
 
 int tiled_box_x() { return BX; }
 int tiled_box_y() { return BY; }

@@ -14,8 +14,8 @@ using lbm::Model;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxRedBlocks = 1024;
-constexpr size_t kRedBytes = (size_t)kMaxRedBlocks * 8 * sizeof(double);
+constexpr int kMaxRedBlocks = 2048;
+constexpr size_t kRedBytes = (size_t)kMaxRedBlocks * 16 * sizeof(double);  // 15 field totals per block
 constexpr size_t kStatusBytes = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -85,6 +85,9 @@ Model<double> make_model(const lbm_vset* v, double tau, double dt, double dx, in
   // lambda_i (Eq. "lp"): c1 dx for the rest particle, c1 dx / 10 for the axis ones
   m.lam0 = dissipation ? c1 * dx * dt / (dx * dx) : 0.0;
   m.lam1 = dissipation ? c1 * dx / 10.0 * dt / (dx * dx) : 0.0;
+  m.keep0 = 1.0 - m.dt_tau - 6.0 * m.lam0;
+  m.keep1 = 1.0 - m.dt_tau - 6.0 * m.lam1;
+  m.keep2 = 1.0 - m.dt_tau;
   return m;
 }
 
@@ -97,6 +100,7 @@ Model<float> to_float(const Model<double>& d) {
   f.Ad0 = (float)d.Ad0; f.AdT = (float)d.AdT; f.AdU = (float)d.AdU;
   f.Bd0 = (float)d.Bd0; f.BdT = (float)d.BdT; f.BdU = (float)d.BdU; f.Dd = (float)d.Dd;
   f.dt_tau = (float)d.dt_tau; f.k1 = (float)d.k1; f.k2 = (float)d.k2; f.lam0 = (float)d.lam0; f.lam1 = (float)d.lam1;
+  f.keep0 = (float)d.keep0; f.keep1 = (float)d.keep1; f.keep2 = (float)d.keep2;
   return f;
 }
 
@@ -123,10 +127,13 @@ struct lbm_sim {
   cudaStream_t st;
   int64_t steps;
   int failed;
+  int fixed_dirty[2];   // FIXED-face layers of buffer b need rewriting
+  int layers_ok[2];     // buffer b's non-FIXED boundary layers match its interior
+  unsigned wait_limit;  // polls of a TMA data wait before the step kernel gives up
   int variant;          // LBM_VARIANT_* of the FP32 step
   int zchunk;           // 0 = automatic
   int num_sms;
-  CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers
+  CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers (box 36 x 12 x 1 x 15)
   // launch counting and event-pair timing
   int64_t launches[LBM_NKERNEL];
   double ms[LBM_NKERNEL];
@@ -157,7 +164,18 @@ int enter(lbm_sim* s) {
   return LBM_OK;
 }
 
-void* spare(lbm_sim* s) { return s->fbuf[s->cur ^ 1]; }
+// The buffer not holding the current state; host-pointer transfers stage
+// through it, which overwrites its boundary layers.
+void* spare(lbm_sim* s) {
+  s->fixed_dirty[s->cur ^ 1] = 1;
+  s->layers_ok[s->cur ^ 1] = 0;
+  return s->fbuf[s->cur ^ 1];
+}
+
+// Faces whose layers change from step to step (all but FIXED), and the FIXED
+// ones, whose layers are written once per buffer when the state is set.
+unsigned step_faces(const lbm_sim* s);
+unsigned fixed_faces(const lbm_sim* s);
 
 constexpr int kRing = 1024;
 
@@ -224,20 +242,23 @@ EncodeTiledFn encode_tiled() {
 }
 
 // 4D map over one FP32 f buffer: (x, y, z, field) with the padded pitches;
-// box = one plane tile with its 2-cell halo, all 15 fields.
-bool make_tmap(CUtensorMap* map, void* base, const Layout& L) {
+// box = one plane tile with its 2-cell halo (bx x by), all 15 fields.
+bool make_tmap(CUtensorMap* map, void* base, const Layout& L, int bx, int by) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)L.sx, (cuuint64_t)(L.ny + 4), (cuuint64_t)(L.nz + 4), (cuuint64_t)lbm::NV};
   const cuuint64_t strides[3] = {(cuuint64_t)L.sx * 4, (cuuint64_t)L.plane * 4, (cuuint64_t)L.fs * 4};
-  const cuuint32_t box[4] = {(cuuint32_t)lbm::tiled_box_x(), (cuuint32_t)lbm::tiled_box_y(), 1, (cuuint32_t)lbm::NV};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)lbm::NV};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// z planes per CTA of the tiled kernel: about four waves of two CTAs per SM.
+// Variants whose step kernel writes the boundary layers of its output.
+bool wt_variant(int variant) { return variant == LBM_VARIANT_TILED; }
+
+// z planes per CTA of the tiled kernels: about four waves of two CTAs per SM.
 int auto_zchunk(const Layout& L, int num_sms) {
   const long long tiles = (long long)((L.nx + lbm::kTileX - 1) / lbm::kTileX) * ((L.ny + lbm::kTileY - 1) / lbm::kTileY);
   const long long want = 4LL * 2 * num_sms;
@@ -248,6 +269,39 @@ int auto_zchunk(const Layout& L, int num_sms) {
   return (int)((L.nz + chunks - 1) / chunks);
 }
 
+unsigned step_faces(const lbm_sim* s) {
+  unsigned m = 0;
+  for (int f = 0; f < 6; ++f)
+    if (s->bc.kind[f] != LBM_BC_FIXED) m |= 1u << f;
+  return m;
+}
+
+unsigned fixed_faces(const lbm_sim* s) { return 0x3fu & ~step_faces(s); }
+
+// Boundary layers the pair kernel writes for the state it produces, and the
+// face mask they cover: periodic axes (x only for even nx, where the boundary
+// cell pairs are whole) and extrapolating / reflecting x faces (even nx).
+lbm::WtDesc write_through(const lbm_sim* s, unsigned* faces) {
+  lbm::WtDesc w;
+  unsigned m = 0;
+  const bool on = wt_variant(s->variant);
+  const bool xeven = (s->L.nx % 2) == 0 && s->L.nx >= 4;
+  const int n[3] = {s->L.nx, s->L.ny, s->L.nz};
+  for (int a = 0; a < 3; ++a) {
+    w.per[a] = on && s->bc.kind[2 * a] == LBM_BC_PERIODIC && n[a] >= 4 && (a != 0 || xeven);
+    if (w.per[a]) m |= 3u << (2 * a);
+  }
+  auto xk = [&](int kind) {
+    return (on && xeven && (kind == LBM_BC_EXTRAPOLATE || kind == LBM_BC_REFLECT)) ? kind : 0;
+  };
+  w.xlo = xk(s->bc.kind[0]);
+  w.xhi = xk(s->bc.kind[1]);
+  if (w.xlo) m |= 1u;
+  if (w.xhi) m |= 2u;
+  if (faces) *faces = m;
+  return w;
+}
+
 }  // namespace
 
 #define LBM_LAUNCH(sim, kind, expr)                        \
@@ -255,6 +309,23 @@ int auto_zchunk(const Layout& L, int num_sms) {
     LBM_CK((sim), begin_launch((sim), (kind)));            \
     LBM_CK((sim), end_launch((sim), (expr)));              \
   } while (0)
+
+namespace {
+
+// FIXED faces hold constant layers: they are written into a buffer once and
+// again only after that buffer served as host staging (which overwrites it).
+int fill_fixed(lbm_sim* s) {
+  const unsigned m = fixed_faces(s);
+  for (int b = 0; b < 2; ++b) {
+    if (!s->fixed_dirty[b]) continue;
+    if (m)
+      LBM_LAUNCH(s, LBM_KERNEL_FILL, lbm::launch_fill(s->prec, s->fbuf[b], s->L, s->md, s->mf, s->bc, m, s->st));
+    s->fixed_dirty[b] = 0;
+  }
+  return LBM_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -324,7 +395,10 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
     s->launches[k] = 0;
     s->ms[k] = 0.0;
   }
+  s->fixed_dirty[0] = s->fixed_dirty[1] = 1;
+  s->layers_ok[0] = s->layers_ok[1] = 0;
   s->variant = LBM_VARIANT_TILED;
+  s->wait_limit = 1u << 22;
   s->zchunk = 0;
   s->num_sms = 0;
   if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
@@ -333,7 +407,9 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
     return LBM_ECUDA;
   }
   if (precision == LBM_FP32) {
-    if (!make_tmap(&s->tmap[0], s->fbuf[0], s->L) || !make_tmap(&s->tmap[1], s->fbuf[1], s->L)) {
+    if (!make_tmap(&s->tmap[0], s->fbuf[0], s->L, lbm::tiled_box_x(), lbm::tiled_box_y()) ||
+        !make_tmap(&s->tmap[1], s->fbuf[1], s->L, lbm::tiled_box_x(), lbm::tiled_box_y()) ||
+        lbm::prepare_tiled_kernels() != cudaSuccess || lbm::prepare_pair_kernels() != cudaSuccess) {
       delete s;
       return LBM_ECUDA;
     }
@@ -365,9 +441,17 @@ int lbm_set_scheme(lbm_sim* s, int32_t scheme, int32_t dissipation) {
 int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk) {
   if (!s) return LBM_EINVAL;
   if (s->failed) return LBM_ESTATE;
-  if ((variant != LBM_VARIANT_TILED && variant != LBM_VARIANT_PLAIN) || zchunk < 0) return LBM_EINVAL;
+  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED_FILL || zchunk < 0) return LBM_EINVAL;
   s->variant = variant;
   s->zchunk = zchunk;
+  s->layers_ok[0] = s->layers_ok[1] = 0;
+  return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_sim* s, uint32_t polls) {
+  if (!s) return LBM_EINVAL;
+  if (s->failed) return LBM_ESTATE;
+  s->wait_limit = polls;
   return LBM_OK;
 }
 
@@ -379,6 +463,8 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, const double* T, in
   s->cur = 0;
   s->steps = 0;
   LBM_CK(s, cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st));
+  s->fixed_dirty[0] = s->fixed_dirty[1] = 1;
+  s->layers_ok[0] = s->layers_ok[1] = 0;
   if (on_device) {
     LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_init(s->prec, s->fbuf[0], s->L, s->md, rho, u, T, s->st));
     return LBM_OK;
@@ -392,28 +478,258 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, const double* T, in
   return LBM_OK;
 }
 
-int lbm_step(lbm_sim* s, int64_t n) {
-  int rc = enter(s);
-  if (rc) return rc;
-  if (n < 0) return LBM_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// n time steps of one sim (fills as needed, then the step kernel).
+int run_steps(lbm_sim* s, int64_t n) {
+  if (n > 0) {
+    int rc = fill_fixed(s);
+    if (rc) return rc;
+  }
+  const bool pair = s->prec == LBM_FP32 && s->variant != LBM_VARIANT_PLAIN && s->variant != LBM_VARIANT_TILED_SINGLE;
+  unsigned wt_faces = 0;
+  const lbm::WtDesc wt = write_through(s, &wt_faces);
   for (int64_t k = 0; k < n; ++k) {
     void* fin = s->fbuf[s->cur];
     void* fout = s->fbuf[s->cur ^ 1];
-    LBM_LAUNCH(s, LBM_KERNEL_FILL, lbm::launch_fill(s->prec, fin, s->L, s->md, s->bc, s->st));
-    if (s->prec == LBM_FP32 && s->variant == LBM_VARIANT_TILED) {
+    // layers the previous step did not write for this state
+    unsigned mask = step_faces(s);
+    if (pair && s->layers_ok[s->cur]) mask &= ~wt_faces;
+    if (mask)
+      LBM_LAUNCH(s, LBM_KERNEL_FILL, lbm::launch_fill(s->prec, fin, s->L, s->md, s->mf, s->bc, mask, s->st));
+    if (s->prec == LBM_FP32 && s->variant != LBM_VARIANT_PLAIN) {
       const int zc = s->zchunk > 0 ? s->zchunk : auto_zchunk(s->L, s->num_sms);
-      LBM_LAUNCH(s, LBM_KERNEL_STEP,
-                 lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf, zc,
-                                        s->flags, s->st));
+      if (pair) {
+        LBM_LAUNCH(s, LBM_KERNEL_STEP,
+                   lbm::launch_step_pair(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf, wt,
+                                         zc, s->flags, s->wait_limit, s->st));
+      } else {
+        LBM_LAUNCH(s, LBM_KERNEL_STEP,
+                   lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf,
+                                          zc, s->flags, s->st));
+      }
     } else {
       LBM_LAUNCH(s, LBM_KERNEL_STEP,
                  lbm::launch_step_plain(s->prec, s->scheme, fin, fout, s->L, s->md, s->mf, s->flags, s->st));
     }
+    s->layers_ok[s->cur ^ 1] = (pair && wt_faces) ? 1 : 0;
     s->cur ^= 1;
     s->steps += 1;
   }
   return LBM_OK;
 }
+
+constexpr int kBatchZchunk = 32;
+
+int batch_check(lbm_sim* const* sims, int32_t n) {
+  if (!sims || n < 1 || n > lbm::kMaxBatch) return LBM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    lbm_sim* s = sims[i];
+    if (!s) return LBM_EINVAL;
+    if (s->failed) return LBM_ESTATE;
+    if (s->prec != LBM_FP32 || s->variant != LBM_VARIANT_TILED) return LBM_EINVAL;
+    if (s->scheme != sims[0]->scheme || s->st != sims[0]->st || s->device != sims[0]->device) return LBM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (sims[j] == s) return LBM_EINVAL;
+  }
+  return LBM_OK;
+}
+
+// n batched time steps: per-sim fills where needed, then one table-driven
+// launch of the persistent tile kernel for all sims.
+int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
+  lbm_sim* s0 = sims[0];
+  for (int i = 0; i < n; ++i) {
+    int rc = fill_fixed(sims[i]);
+    if (rc) return rc;
+  }
+  thread_local static lbm::BatchTable tab;  // built on the host, passed by value to the kernel
+  unsigned wt_faces[lbm::kMaxBatch];
+  lbm::WtDesc wt[lbm::kMaxBatch];
+  for (int i = 0; i < n; ++i) wt[i] = write_through(sims[i], &wt_faces[i]);
+  for (int64_t k = 0; k < steps; ++k) {
+    long long units = 0;
+    for (int i = 0; i < n; ++i) {
+      lbm_sim* s = sims[i];
+      unsigned mask = step_faces(s);
+      if (s->layers_ok[s->cur]) mask &= ~wt_faces[i];
+      if (mask)
+        LBM_LAUNCH(s, LBM_KERNEL_FILL,
+                   lbm::launch_fill(s->prec, s->fbuf[s->cur], s->L, s->md, s->mf, s->bc, mask, s->st));
+      lbm::BatchItem& it = tab.item[i];
+      tab.map[i] = s->tmap[s->cur];
+      it.fin = (const float*)s->fbuf[s->cur];
+      it.fout = (float*)s->fbuf[s->cur ^ 1];
+      it.flags = s->flags;
+      it.L = s->L;
+      it.m = s->mf;
+      it.wt = wt[i];
+      it.tiles_x = (s->L.nx + lbm::kTileX - 1) / lbm::kTileX;
+      it.tiles_y = (s->L.ny + lbm::kTileY - 1) / lbm::kTileY;
+      it.zc = s->zchunk > 0 ? s->zchunk : kBatchZchunk;
+      it.first_unit = units;
+      units += (long long)it.tiles_x * it.tiles_y * ((s->L.nz + it.zc - 1) / it.zc);
+    }
+    tab.n = n;
+    tab.wait_limit = s0->wait_limit;
+    tab.total_units = units;
+    const long long resident = 2LL * s0->num_sms;  // two CTAs per SM
+    const int grid = (int)(units < resident ? units : resident);
+    LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(s0->scheme, tab, grid, s0->st));
+    for (int i = 0; i < n; ++i) {
+      lbm_sim* s = sims[i];
+      s->layers_ok[s->cur ^ 1] = 1;
+      s->cur ^= 1;
+      s->steps += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+struct lbm_graph {
+  cudaGraphExec_t exec;
+  cudaStream_t st;
+  int n;
+  lbm_sim* sims[lbm::kMaxBatch];
+  int cur[lbm::kMaxBatch];
+  int64_t steps;
+  int64_t launches[LBM_NKERNEL];  // per replay, booked on sims[0]
+};
+
+extern "C" {
+
+int lbm_step(lbm_sim* s, int64_t n) {
+  int rc = enter(s);
+  if (rc) return rc;
+  if (n < 0) return LBM_EINVAL;
+  return run_steps(s, n);
+}
+
+int lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
+  int rc = batch_check(sims, n);
+  if (rc) return rc;
+  rc = enter(sims[0]);
+  if (rc) return rc;
+  if (steps < 0) return LBM_EINVAL;
+  return run_batch(sims, n, steps);
+}
+
+int lbm_graph_capture(lbm_sim* const* sims, int32_t n, int64_t steps, lbm_graph** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!sims || n < 1 || steps < 2 || steps % 2) return LBM_EINVAL;
+  int rc = n == 1 ? (sims[0] ? LBM_OK : LBM_EINVAL) : batch_check(sims, n);
+  if (rc) return rc;
+  lbm_sim* s0 = sims[0];
+  rc = enter(s0);
+  if (rc) return rc;
+  // boundary layers that only need writing once are written now, outside the graph
+  for (int i = 0; i < n; ++i) {
+    lbm_sim* s = sims[i];
+    rc = fill_fixed(s);
+    if (rc) return rc;
+    if (!s->layers_ok[s->cur]) {
+      const unsigned mask = step_faces(s);
+      if (mask)
+        LBM_LAUNCH(s, LBM_KERNEL_FILL, lbm::launch_fill(s->prec, s->fbuf[s->cur], s->L, s->md, s->mf, s->bc, mask,
+                                                        s->st));
+      s->layers_ok[s->cur] = s->prec == LBM_FP32 && wt_variant(s->variant);
+    }
+  }
+  lbm_graph* g = new (std::nothrow) lbm_graph();
+  if (!g) return LBM_ENOMEM;
+  g->st = s0->st;
+  g->n = n;
+  g->steps = steps;
+  // the capture records launches without running them: save the host-side
+  // state it advances and restore it afterwards
+  int64_t saved_steps[lbm::kMaxBatch], saved_launch[lbm::kMaxBatch][LBM_NKERNEL];
+  int saved_timing[lbm::kMaxBatch], saved_ok[lbm::kMaxBatch][2];
+  for (int i = 0; i < n; ++i) {
+    lbm_sim* s = sims[i];
+    g->sims[i] = s;
+    g->cur[i] = s->cur;
+    saved_steps[i] = s->steps;
+    saved_timing[i] = s->timing;
+    saved_ok[i][0] = s->layers_ok[0];
+    saved_ok[i][1] = s->layers_ok[1];
+    for (int k = 0; k < LBM_NKERNEL; ++k) saved_launch[i][k] = s->launches[k];
+    s->timing = 0;
+  }
+  // capture on a private stream (the sims' stream may be the legacy default
+  // stream, which cannot be captured); replays run on the sims' stream
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < n; ++i) sims[i]->st = cap;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = n == 1 ? run_steps(s0, steps) : run_batch(sims, n, steps);
+      cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    for (int i = 0; i < n; ++i) sims[i]->st = g->st;
+    cudaStreamDestroy(cap);
+  }
+  for (int k = 0; k < LBM_NKERNEL; ++k) g->launches[k] = s0->launches[k] - saved_launch[0][k];
+  if (n > 1)
+    for (int i = 1; i < n; ++i)
+      for (int k = 0; k < LBM_NKERNEL; ++k) g->launches[k] += sims[i]->launches[k] - saved_launch[i][k];
+  for (int i = 0; i < n; ++i) {
+    lbm_sim* s = sims[i];
+    s->steps = saved_steps[i];
+    s->timing = saved_timing[i];
+    s->cur = g->cur[i];
+    s->layers_ok[0] = saved_ok[i][0];
+    s->layers_ok[1] = saved_ok[i][1];
+    for (int k = 0; k < LBM_NKERNEL; ++k) s->launches[k] = saved_launch[i][k];
+  }
+  if (e == cudaSuccess && rc == LBM_OK) e = cudaGraphInstantiate(&g->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != LBM_OK || e != cudaSuccess) {
+    delete g;
+    if (rc != LBM_OK) return rc;
+    for (int i = 0; i < n; ++i) sims[i]->failed = 1;
+    return LBM_ECUDA;
+  }
+  *out = g;
+  return LBM_OK;
+}
+
+int lbm_graph_launch(lbm_graph* g) {
+  if (!g) return LBM_EINVAL;
+  for (int i = 0; i < g->n; ++i) {
+    if (g->sims[i]->failed) return LBM_ESTATE;
+    if (g->sims[i]->cur != g->cur[i]) return LBM_ESTATE;
+  }
+  lbm_sim* s0 = g->sims[0];
+  int rc = enter(s0);
+  if (rc) return rc;
+  LBM_CK(s0, cudaGraphLaunch(g->exec, g->st));
+  for (int i = 0; i < g->n; ++i) {
+    lbm_sim* s = g->sims[i];
+    s->steps += g->steps;
+    if (s->prec == LBM_FP32 && wt_variant(s->variant)) s->layers_ok[s->cur] = 1;
+  }
+  for (int k = 0; k < LBM_NKERNEL; ++k) s0->launches[k] += g->launches[k];
+  return LBM_OK;
+}
+
+void lbm_graph_destroy(lbm_graph* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->st);
+  cudaGraphExecDestroy(g->exec);
+  delete g;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int lbm_moments(lbm_sim* s, double* rho, double* u, double* T, int32_t on_device) {
   int rc = enter(s);
@@ -457,6 +773,8 @@ int lbm_set_f(lbm_sim* s, const void* f, int32_t on_device) {
   s->cur = 0;
   s->steps = 0;
   LBM_CK(s, cudaMemsetAsync(s->flags, 0, sizeof(unsigned), s->st));
+  s->fixed_dirty[0] = s->fixed_dirty[1] = 1;
+  s->layers_ok[0] = s->layers_ok[1] = 0;
   if (on_device) {
     LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_unpack(s->prec, s->fbuf[0], s->L, f, s->st));
     return LBM_OK;

@@ -53,6 +53,9 @@ struct Model {
   R dt_tau;   // dt / tau
   R k1, k2;   // c1 dt/dx, (c2/sqrt 3) dt/dx
   R lam0, lam1;  // lambda_i dt/dx^2 for i = 0 and i = 1..6 (0 when the term is off)
+  // coefficient of f_i in the update once relaxation and the centre of the
+  // Laplacian are folded in: 1 - dt/tau - 6 lambda_i dt/dx^2 (rest, axis, diagonal)
+  R keep0, keep1, keep2;
 };
 
 struct BcDesc {
@@ -60,54 +63,83 @@ struct BcDesc {
   double fixed[6][5];   // (rho,u1,u2,u3,T)
 };
 
+// Boundary layers a step kernel writes itself for the state it produces
+// ("write-through"), so that no fill kernel runs before the next step:
+// periodic images along each flagged axis, and the extrapolated / reflected
+// layers of the x faces (kind LBM_BC_EXTRAPOLATE or LBM_BC_REFLECT, 0 = not
+// handled in the kernel).
+struct WtDesc {
+  int per[3];
+  int xlo, xhi;
+};
+
 // ---------------------------------------------------------------- physics
+
+// Explicitly rounded arithmetic.  Every product, sum and fused multiply-add
+// below is spelled out, so the compiler contracts nothing on its own and the
+// same expression rounds identically in every kernel that inlines it (the
+// fill kernel, the step kernels, the write-through of the boundary layers,
+// and the batched step).  The order matches the packed-pair step kernel.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Moments of 15 values (relations e1-e3): rho, u, T with
 // E = eta0^2 f0 + c1^2 sum_{axis} f + c2^2 sum_{diag} f, T = (E/rho - u^2)/b.
 template <typename R, typename M>
-__host__ __device__ __forceinline__ void moments(const M& m, const R f[NV], R& rho, R& ux, R& uy, R& uz, R& T) {
-  const R sa = ((f[1] + f[2]) + (f[3] + f[4])) + (f[5] + f[6]);
-  const R dpp = f[7] + f[8], dpm = f[9] + f[10], dmp = f[11] + f[12], dmm = f[13] + f[14];
-  const R sd = (dpp + dpm) + (dmp + dmm);
-  rho = f[0] + sa + sd;
-  const R mx = m.c1 * (f[1] - f[2]) + m.s * ((dpp + dpm) - (dmp + dmm));
-  const R my = m.c1 * (f[3] - f[4]) + m.s * ((dpp + dmp) - (dpm + dmm));
-  const R mz = m.c1 * (f[5] - f[6]) + m.s * (((f[7] + f[9]) + (f[11] + f[13])) - ((f[8] + f[10]) + (f[12] + f[14])));
-  const R E = m.eta0sq * f[0] + m.c1sq * sa + m.c2sq * sd;
+__device__ __forceinline__ void moments(const M& m, const R f[NV], R& rho, R& ux, R& uy, R& uz, R& T) {
+  const R sa = radd(radd(radd(f[1], f[2]), radd(f[3], f[4])), radd(f[5], f[6]));
+  const R dpp = radd(f[7], f[8]), dpm = radd(f[9], f[10]), dmp = radd(f[11], f[12]), dmm = radd(f[13], f[14]);
+  const R sd = radd(radd(dpp, dpm), radd(dmp, dmm));
+  rho = radd(radd(f[0], sa), sd);
+  const R mx = rfma(R(m.c1), rsub(f[1], f[2]), rmul(R(m.s), rsub(radd(dpp, dpm), radd(dmp, dmm))));
+  const R my = rfma(R(m.c1), rsub(f[3], f[4]), rmul(R(m.s), rsub(radd(dpp, dmp), radd(dpm, dmm))));
+  const R mz = rfma(R(m.c1), rsub(f[5], f[6]),
+                    rmul(R(m.s), rsub(radd(radd(f[7], f[9]), radd(f[11], f[13])),
+                                      radd(radd(f[8], f[10]), radd(f[12], f[14])))));
+  const R E = rfma(R(m.eta0sq), f[0], rfma(R(m.c1sq), sa, rmul(R(m.c2sq), sd)));
   const R ir = R(1) / rho;
-  ux = mx * ir;
-  uy = my * ir;
-  uz = mz * ir;
-  T = (E * ir - (ux * ux + uy * uy + uz * uz)) * m.inv_b;
+  ux = rmul(mx, ir);
+  uy = rmul(my, ir);
+  uz = rmul(mz, ir);
+  const R usq = rfma(ux, ux, rfma(uy, uy, rmul(uz, uz)));
+  T = rmul(rsub(rmul(E, ir), usq), R(m.inv_b));
 }
 
 // f^eq_i = rho (A_i + B_i w + D_i w^2), w = v_i . u (Eq. "eq").
 template <typename R, typename M>
-__host__ __device__ __forceinline__ void equilibrium(const M& m, R rho, R ux, R uy, R uz, R T, R feq[NV]) {
-  const R usq = ux * ux + uy * uy + uz * uz;
-  feq[0] = rho * (m.AR * T);
-  const R Aa = m.Aa0 + m.AaT * T + m.AaU * usq;
-  const R Ba = m.Ba0 + m.BaT * T + m.BaU * usq;
+__device__ __forceinline__ void equilibrium(const M& m, R rho, R ux, R uy, R uz, R T, R feq[NV]) {
+  const R usq = rfma(ux, ux, rfma(uy, uy, rmul(uz, uz)));
+  feq[0] = rmul(rho, rmul(R(m.AR), T));
+  const R Aa = rfma(R(m.AaT), T, rfma(R(m.AaU), usq, R(m.Aa0)));
+  const R Ba = rfma(R(m.BaT), T, rfma(R(m.BaU), usq, R(m.Ba0)));
   const R u3[3] = {ux, uy, uz};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const R w = m.c1 * u3[a];
-    const R q = Aa + m.Da * (w * w);
-    const R l = Ba * w;
-    feq[1 + 2 * a] = rho * (q + l);
-    feq[2 + 2 * a] = rho * (q - l);
+    const R w = rmul(R(m.c1), u3[a]);
+    const R q = rfma(R(m.Da), rmul(w, w), Aa);
+    const R l = rmul(Ba, w);
+    feq[1 + 2 * a] = rmul(rho, radd(q, l));
+    feq[2 + 2 * a] = rmul(rho, rsub(q, l));
   }
-  const R Ad = m.Ad0 + m.AdT * T + m.AdU * usq;
-  const R Bd = m.Bd0 + m.BdT * T + m.BdU * usq;
+  const R Ad = rfma(R(m.AdT), T, rfma(R(m.AdU), usq, R(m.Ad0)));
+  const R Bd = rfma(R(m.BdT), T, rfma(R(m.BdU), usq, R(m.Bd0)));
   // k = 0..3 are (+ + +), (+ + -), (+ - +), (+ - -); k and 7-k are opposite
-  const R w4[4] = {m.s * ((ux + uy) + uz), m.s * ((ux + uy) - uz), m.s * ((ux - uy) + uz), m.s * ((ux - uy) - uz)};
+  const R sxy = radd(ux, uy), dxy = rsub(ux, uy);
+  const R w4[4] = {rmul(R(m.s), radd(sxy, uz)), rmul(R(m.s), rsub(sxy, uz)), rmul(R(m.s), radd(dxy, uz)),
+                   rmul(R(m.s), rsub(dxy, uz))};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const R w = w4[k];
-    const R q = Ad + m.Dd * (w * w);
-    const R l = Bd * w;
-    feq[7 + k] = rho * (q + l);
-    feq[14 - k] = rho * (q - l);
+    const R q = rfma(R(m.Dd), rmul(w, w), Ad);
+    const R l = rmul(Bd, w);
+    feq[7 + k] = rmul(rho, radd(q, l));
+    feq[14 - k] = rmul(rho, rsub(q, l));
   }
 }
 
@@ -142,7 +174,9 @@ __device__ __forceinline__ R grad_neg(R m1, R c, R p1, R p2) {
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after enqueueing on `st`.
 
-cudaError_t launch_fill(int prec, void* f, const Layout& L, const Model<double>& m, const BcDesc& bc, cudaStream_t st);
+// Boundary layers of the faces whose bit (2*axis + hi) is set in mask.
+cudaError_t launch_fill(int prec, void* f, const Layout& L, const Model<double>& md, const Model<float>& mf,
+                        const BcDesc& bc, unsigned mask, cudaStream_t st);
 cudaError_t launch_init(int prec, void* f, const Layout& L, const Model<double>& m, const double* rho,
                         const double* u, const double* T, cudaStream_t st);
 cudaError_t launch_moments(int prec, const void* f, const Layout& L, const Model<double>& m, double* rho, double* u,
@@ -155,6 +189,39 @@ cudaError_t launch_step_plain(int prec, int scheme, const void* fin, void* fout,
                               const Model<double>& md, const Model<float>& mf, unsigned* flags, cudaStream_t st);
 cudaError_t launch_step_tiled(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
                               const Model<float>& m, int zc, unsigned* flags, cudaStream_t st);
+// Pair kernel: the tiles and TMA box of the tiled kernel (kTileX x kTileY,
+// box tiled_box_x() x tiled_box_y()), two cells per thread.
+cudaError_t launch_step_pair(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
+                             const Model<float>& m, const WtDesc& wt, int zc, unsigned* flags, unsigned wait_limit,
+                             cudaStream_t st);
+
+// Descriptor table of a batched step (passed by value as the kernel
+// parameter): one entry per grid, units [first_unit, first_unit +
+// tiles_x * tiles_y * ceil(nz / zc)) in z-chunk-major order.
+constexpr int kMaxBatch = 48;
+struct BatchItem {
+  const float* fin;
+  float* fout;
+  unsigned* flags;
+  Layout L;
+  Model<float> m;
+  WtDesc wt;
+  int tiles_x, tiles_y, zc;
+  long long first_unit;
+};
+struct BatchTable {
+  CUtensorMap map[kMaxBatch];
+  BatchItem item[kMaxBatch];
+  int n;
+  unsigned wait_limit;
+  long long total_units;
+};
+// Batched step over the descriptor table (same tiles and box).
+cudaError_t launch_step_pair_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st);
+// Shared-memory attributes of the tiled kernels; set once per device before
+// their first launch (not allowed inside a stream capture).
+cudaError_t prepare_tiled_kernels();
+cudaError_t prepare_pair_kernels();
 // Geometry of the tiled kernel's TMA box (x, y extents) and CTA tile.
 int tiled_box_x();
 int tiled_box_y();

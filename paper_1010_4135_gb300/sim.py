@@ -84,9 +84,12 @@ class Sim:
         A.check(A.lbm_set_scheme(self._h, s, int(bool(dissipation))), "lbm_set_scheme")
 
     def set_launch(self, variant="tiled", zchunk: int = 0):
-        """FP32 step kernel: "tiled" (TMA plane tiles, default) or "plain"; zchunk = z planes per CTA (0 = auto)."""
-        v = {"tiled": A.LBM_VARIANT_TILED, "plain": A.LBM_VARIANT_PLAIN}[variant] if isinstance(variant, str) \
-            else int(variant)
+        """FP32 step kernel: "tiled" (32 x 8 TMA plane tiles, cell pairs, boundary layers
+        written by the step; default), "tiled_fill" (boundary layers by a fill launch),
+        "tiled_single" (one cell per thread) or "plain"; zchunk = z planes per CTA (0 = auto)."""
+        v = {"tiled": A.LBM_VARIANT_TILED, "plain": A.LBM_VARIANT_PLAIN,
+             "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL}[variant] \
+            if isinstance(variant, str) else int(variant)
         A.check(A.lbm_set_launch(self._h, v, int(zchunk)), "lbm_set_launch")
 
     def init(self, rho, u, T):
@@ -171,6 +174,46 @@ class Sim:
         if rc not in (A.LBM_OK, A.LBM_ENONFINITE, A.LBM_ETIMEOUT):
             raise A.LbmError(rc, "lbm_health")
         return int(flags.value)
+
+
+def _handles(sims):
+    arr = (ctypes.c_void_p * len(sims))()
+    for k, s in enumerate(sims):
+        arr[k] = s.handle
+    return arr
+
+
+def step_batch(sims, steps: int = 1):
+    """Advance FP32 sims together: one persistent tile-kernel launch per step
+    covers all of them (lbm_step_batch)."""
+    A.check(A.lbm_step_batch(_handles(sims), len(sims), int(steps)), "lbm_step_batch")
+
+
+class Graph:
+    """A captured CUDA graph of `steps` (even) steps of one sim or a batch."""
+
+    def __init__(self, sims, steps: int):
+        self.sims = list(sims)
+        self.steps = int(steps)
+        h = ctypes.c_void_p()
+        A.check(A.lbm_graph_capture(_handles(self.sims), len(self.sims), self.steps, ctypes.byref(h)),
+                "lbm_graph_capture")
+        self._h = h
+
+    def launch(self, times: int = 1):
+        for _ in range(int(times)):
+            A.check(A.lbm_graph_launch(self._h), "lbm_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            A.lbm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, precision="fp64", **kw) -> Sim:

@@ -1,0 +1,47 @@
+"""The continuous-batching server: requests admitted as they arrive and as
+memory frees up, stepped together, each result bitwise the same as the
+request solved alone."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _trace():
+    grids = ((16, 16, 16), (24, 16, 16), (20, 12, 12), (32, 16, 8))
+    tr = workloads.serving_trace(seed=7, n=8, rate=200.0, grids=grids, steps=(20, 70))
+    return tr
+
+
+def test_served_results_equal_alone_and_budget_is_respected():
+    from paper_1010_4135_gb300 import serve
+    from paper_1010_4135_gb300 import sim as S
+    tr = _trace()
+    sizes = [serve.workspace_bytes(r["grid"]) for r in tr]
+    budget = 2 * max(sizes) + min(sizes)  # forces waiting for memory to free up
+    srv = serve.Server(hbm_budget=budget, max_batch=3, tick=16, keep_results=True)
+    done = srv.run(tr)
+    assert len(done) == len(tr)
+    assert srv.peak_bytes <= budget and srv.peak_batch <= 3
+    assert all(j.health == 0 for j in done)
+    # requests overlapped on the device: some batch held more than one grid
+    assert srv.peak_batch >= 2
+    for j in done:
+        w = workloads.request_workload(j.req, *j.params)
+        s = S.from_workload(w, precision="fp32")
+        rho, u, T = w.initial_fields()
+        s.init(rho, u, T)
+        s.step(j.req["steps"])
+        alone, _, _ = s.moments()
+        assert np.array_equal(alone, j.rho), j.req
+    st = serve.summary(done, srv.wall)
+    assert st["p50_latency_s"] <= st["p99_latency_s"]

@@ -177,12 +177,13 @@ def shock_droplet(n=256):
                         2.0, 6.0, 4.0, 5e-5, 5e-5, 2000)
 
 
-def shock_bubble(nx=512, ny=256, nz=256, mach=3.0):
+def shock_bubble(nx=512, ny=256, nz=256, mach=3.0, c=(4.0, 12.0, 8.0), dt=2e-5):
     """Mach-3 shock into a rho = 0.1 bubble (radius 0.15, centre (0.35, 0.5,
-    0.5)), 512x256x256 cells of 1/256; (c1, c2, eta0) = (4, 12, 8), dt = tau = 2e-5."""
+    0.5)), 512x256x256 cells of 1/256; (c1, c2, eta0) = (4, 12, 8), dt = tau = 2e-5
+    unless given."""
     dx = 1.0 / ny
     return shock_sphere(f"shock_bubble_{nx}x{ny}x{nz}", nx, ny, nz, dx, mach, 0.1, 0.15, (0.35, 0.5, 0.5),
-                        4.0, 12.0, 8.0, 2e-5, 2e-5, 2000)
+                        c[0], c[1], c[2], dt, dt, 2000)
 
 
 def batch_machs(seed: int = 4, n: int = 8):
@@ -213,3 +214,60 @@ def smooth_random_fields(nx, ny, nz, seed: int, rho0=1.0, u0=(0.3, -0.2, 0.1), T
     u = np.stack([u0[a] + amp * field() for a in range(3)])
     T = T0 * (1.0 + amp * field())
     return rho, u, T
+
+
+# ---------------------------------------------------------------- serving trace
+
+SERVING_GRIDS = ((64, 64, 64), (96, 96, 96), (128, 128, 128), (192, 128, 128), (256, 256, 256))
+
+
+def serving_trace(seed: int = 5, n: int = 200, rate: float = 20.0, grids=SERVING_GRIDS,
+                  steps=(500, 3000), mach=(1.2, 10.0), ratio=(0.1, 10.0)):
+    """Seeded request stream: exponential inter-arrival times of mean 1/rate,
+    grid uniform over `grids`, Mach uniform, density ratio log-uniform, step
+    count uniform in [steps[0], steps[1]], kind 50/50 shock tube or shock
+    sphere.  Returns a list of dicts sorted by arrival time (seconds)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for k in range(n):
+        g = grids[int(rng.integers(0, len(grids)))]
+        out.append({
+            "id": k,
+            "arrival": float(t[k]),
+            "grid": tuple(int(v) for v in g),
+            "mach": float(rng.uniform(*mach)),
+            "ratio": float(10.0 ** rng.uniform(math.log10(ratio[0]), math.log10(ratio[1]))),
+            "steps": int(rng.integers(steps[0], steps[1] + 1)),
+            "kind": "tube" if rng.uniform() < 0.5 else "sphere",
+        })
+    return out
+
+
+def request_states(req):
+    """Pre-shock, post-shock and second-gas states (rho, u1, u2, u3, T) of a
+    request: a shock of the request's Mach number into gas at rest (1, 0, p=1),
+    and gas of density `ratio` at the same pressure (the tube's right state or
+    the sphere)."""
+    r2, u2, p2, _ = rankine_hugoniot(req["mach"])
+    pre = state_from_p(1.0, 0.0, 0.0, 0.0, 1.0)
+    post = state_from_p(r2, u2, 0.0, 0.0, p2)
+    other = state_from_p(req["ratio"], 0.0, 0.0, 0.0, 1.0)
+    return pre, post, other
+
+
+def request_workload(req, c1, c2, eta0, dt):
+    """The Workload of a request with the given model constants.  Tube: the
+    post-shock state (x < 0.3 of the domain) against gas of the request's
+    density ratio; sphere: the shock entering at x = 0 into ambient gas holding
+    a sphere of that density (radius 0.1 L_y, centre (0.3 L_x, 0.5, 0.5))."""
+    nx, ny, nz = req["grid"]
+    dx = 1.0 / ny
+    pre, post, other = request_states(req)
+    if req["kind"] == "tube":
+        w = shock_tube(f"req{req['id']}_tube", nx, ny, nz, dx, post, other, 0.3 * nx * dx, c1, c2, eta0, dt, dt,
+                       req["steps"])
+    else:
+        w = shock_sphere(f"req{req['id']}_sphere", nx, ny, nz, dx, req["mach"], req["ratio"], 0.1,
+                         (0.3 * nx * dx, 0.5, 0.5), c1, c2, eta0, dt, dt, req["steps"])
+    return w
