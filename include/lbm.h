@@ -128,6 +128,17 @@ LBM_API int lbm_set_scheme(lbm_sim* sim, int32_t scheme, int32_t dissipation);
  * FP64 sims always use the plain kernel. */
 LBM_API int lbm_set_launch(lbm_sim* sim, int32_t variant, int32_t zchunk);
 
+/* FP64 temperature recovery of the FP32 tiled step (LBM_VARIANT_TILED and
+ * lbm_step_batch).  The FP32 T = (E/rho - u^2)/b of Sec. 2 subtracts large
+ * terms when c1^2 >> T (the equilibrium's axis and diagonal populations are
+ * then large and of opposite sign); its relative rounding error is about
+ * 2^-24 kappa with kappa = 1 + (6 c1^2 |A_axis| + 8 c2^2 |A_diag| + u^2)/(b T).
+ * Cells with kappa > kappa_max, or with T <= 0 in FP32, recompute rho, u and
+ * T from their 15 values in FP64.  kappa_max = 0 turns it off; otherwise
+ * kappa_max >= 1 (LBM_EINVAL else).  The paper has no counterpart: it fixes
+ * no precision. */
+LBM_API int lbm_set_t_recovery(lbm_sim* sim, double kappa_max);
+
 /* Polls the tiled step kernels make on a shared-memory copy barrier before
  * giving up (default 2^22, seconds of waiting).  On giving up a kernel sets
  * LBM_HEALTH_TIMEOUT, lets its copies in flight finish (with the default

@@ -47,6 +47,7 @@ SIGNATURES = [
     ("lbm_set_scheme", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("lbm_set_launch", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     ("lbm_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint32]),
+    ("lbm_set_t_recovery", ctypes.c_int, [_vp, ctypes.c_double]),
     ("lbm_init", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
     ("lbm_step", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("lbm_step_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int64]),
@@ -113,6 +114,7 @@ lbm_create = _forward("lbm_create")
 lbm_set_scheme = _forward("lbm_set_scheme")
 lbm_set_launch = _forward("lbm_set_launch")
 lbm_set_wait_limit = _forward("lbm_set_wait_limit")
+lbm_set_t_recovery = _forward("lbm_set_t_recovery")
 lbm_init = _forward("lbm_init")
 lbm_step = _forward("lbm_step")
 lbm_step_batch = _forward("lbm_step_batch")

@@ -1,0 +1,128 @@
+"""Launch-configuration autotuner of the FP32 step.
+
+The knob is the z chunk of the tiled pair kernel (planes one CTA marches):
+long chunks re-read fewer boundary planes, short chunks fill the SMs and
+balance the tail.  The best value depends on the grid's shape and the SM
+count, so it is measured: each candidate runs a few steps of the sim's own
+state on a scratch copy of the sim (its own workspace, so the user's state
+and step count are untouched), timed with CUDA events on the scratch sim's
+stream; the fastest is applied and cached per (device, grid, precision,
+scheme, boundary kinds) in a JSON file (LBM_TUNE_CACHE, default
+~/.cache/paper_1010_4135_gb300/launch.json), so each shape is tuned once.
+FP64 sims always use the plain kernel and are not tuned.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+ZCHUNKS = (4, 8, 12, 16, 24, 32, 48)
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    return os.environ.get("LBM_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "paper_1010_4135_gb300", "launch.json")
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, key, value):
+    with _lock:
+        data = _load(path)
+        data[key] = value
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def key_of(sims, batched: bool, device_name: str | None = None, sms: int | None = None) -> str:
+    """Cache key: device, SM count, and per sim the grid, precision, scheme and boundary kinds."""
+    if device_name is None or sms is None:
+        props = torch.cuda.get_device_properties(sims[0].device)
+        device_name, sms = props.name, props.multi_processor_count
+    parts = [device_name.replace(" ", "_"), str(int(sms)), "batch" if batched else "single"]
+    for s in sims:
+        c = s.config
+        parts.append("x".join(str(int(v)) for v in (c["nx"], c["ny"], c["nz"])) + f":{c['precision']}:{c['scheme']}:"
+                     + "".join(str(int(k)) for k in tuple(c["bc_lo"]) + tuple(c["bc_hi"])))
+    return "|".join(parts)
+
+
+def _time(run, steps: int, warmup: int) -> float:
+    run(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run(steps)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bool = False) -> dict:
+    """{zchunk: ms per step} of the given sims' current states on scratch copies."""
+    from . import sim as S
+    scratch = []
+    try:
+        with torch.cuda.stream(torch.cuda.Stream(device=sims[0].device)):
+            for s in sims:
+                f = torch.empty((15,) + s.shape, dtype=torch.float32, device=s.device)
+                s.sync()
+                s.get_f(out=f)
+                s.sync()
+                c = s.clone(stream=torch.cuda.current_stream(s.device))
+                scratch.append((c, f))
+            out = {}
+            for zc in zchunks:
+                for c, f in scratch:
+                    c.set_launch("tiled", zc)
+                    c.set_f(f)
+                if batched:
+                    run = lambda n: S.step_batch([c for c, _ in scratch], n)
+                else:
+                    run = scratch[0][0].step
+                out[int(zc)] = _time(run, steps, warmup)
+            return out
+    finally:
+        for c, _ in scratch:
+            c.close()
+
+
+def tune(sim, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None) -> dict:
+    """Choose and apply the z chunk of one FP32 sim; returns {"zchunk", "ms", "cached", "timings"}."""
+    return _tune([sim], zchunks, steps, use_cache, path, batched=False)
+
+
+def tune_batch(sims, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None) -> dict:
+    """Choose and apply one z chunk for sims stepped together (lbm_step_batch)."""
+    return _tune(list(sims), zchunks, steps, use_cache, path, batched=True)
+
+
+def _tune(sims, zchunks, steps, use_cache, path, batched, key=None):
+    if any(s.config["precision"] not in ("fp32", 1) for s in sims):
+        return {"zchunk": None, "ms": None, "cached": False, "timings": {}}
+    path = path or cache_path()
+    key = key or key_of(sims, batched)
+    hit = _load(path).get(key) if use_cache else None
+    if hit is not None:
+        for s in sims:
+            s.set_launch("tiled", int(hit["zchunk"]))
+        return {**hit, "cached": True}
+    timings = measure(sims, zchunks, steps, batched=batched)
+    best = min(timings, key=timings.get)
+    for s in sims:
+        s.set_launch("tiled", best)
+    rec = {"zchunk": best, "ms": timings[best], "timings": {str(k): v for k, v in timings.items()}}
+    _store(path, key, rec)
+    return {**rec, "cached": False}

@@ -203,60 +203,75 @@ struct FieldAcc<float> {
 
 // Deterministic FP64 global sums of (rho, rho u, E) over interior cells.  The
 // moments are linear in f, so the kernel sums each field f_i over the cells
-// (a fixed grid-stride assignment, a fixed shared-memory tree per block) and
-// the last block to finish adds the per-block field totals in block order and
-// combines them: mass = sum_i F_i, momentum = sum_i v_i F_i, energy =
-// sum_i (v_i^2 + eta_i^2) F_i.
+// and combines the 15 field totals at the end: mass = sum_i F_i, momentum =
+// sum_i v_i F_i, energy = sum_i (v_i^2 + eta_i^2) F_i.  Each warp takes
+// whole x rows (global warp w: rows w, w + W, ...; lanes stride x by 32, so
+// every field load is a coalesced 128-byte line); warps reduce by a fixed
+// shuffle tree, blocks by warp order, and the last block to finish sums the
+// per-block totals with all its threads in a fixed split (16 strided
+// partial sums per field, then in order).  The order never depends on
+// timing, so the result is bitwise reproducible.
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restrict__ f, Layout L, Model<double> m,
                                                                 double* __restrict__ partials,
                                                                 unsigned* __restrict__ counter,
                                                                 double* __restrict__ result,
                                                                 unsigned* __restrict__ flags) {
-  __shared__ double sh[RED_THREADS];
-  __shared__ double tot[NV];
+  constexpr int WARPS = RED_THREADS / 32;
+  __shared__ double wsum[WARPS][16];
+  __shared__ double part[16][16];
   __shared__ bool last;
   FieldAcc<R> acc;
   bool bad = false;
-  const long long n = L.ncell();
-  for (long long k = (long long)blockIdx.x * RED_THREADS + threadIdx.x; k < n; k += (long long)gridDim.x * RED_THREADS) {
-    int x, y, z;
-    cell_of(L, k, x, y, z);
-    const long long idx = L.at(x, y, z);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nrows = L.ny * L.nz;
+  const int nw = gridDim.x * WARPS;
+  for (int r = blockIdx.x * WARPS + warp; r < nrows; r += nw) {
+    const long long row = L.at(0, r % L.ny, r / L.ny);
+    for (int x = lane; x < L.nx; x += 32) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const R v = f[i * L.fs + idx];
-      bad |= !finite_value(v);
-      acc.add(i, v);
+      for (int i = 0; i < NV; ++i) {
+        const R v = f[i * L.fs + row + x];
+        bad |= !finite_value(v);
+        acc.add(i, v);
+      }
     }
   }
   if (bad) atomicOr(flags, (unsigned)LBM_HEALTH_NONFINITE);
-  for (int i = 0; i < NV; ++i) {
-    sh[threadIdx.x] = acc.value(i);
-    __syncthreads();
-    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) tot[i] = sh[0];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) partials[blockIdx.x * 16 + i] = tot[i];
-    __threadfence();
-    const unsigned done = atomicAdd(counter, 1u);
-    last = (done == gridDim.x - 1);
+  for (int i = 0; i < NV; ++i) {
+    double v = acc.value(i);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) wsum[warp][i] = v;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) t += wsum[w][threadIdx.x];
+    partials[blockIdx.x * 16 + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  {
+    const int i = threadIdx.x & 15, j = threadIdx.x >> 4;  // field i, strided part j of 16
+    double t = 0.0;
+    if (i < NV)
+      for (unsigned b = j; b < gridDim.x; b += 16) t += ((volatile double*)partials)[b * 16 + i];
+    part[j][i] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double F[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) F[i] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) F[i] += ((volatile double*)partials)[b * 16 + i];
+    for (int i = 0; i < NV; ++i) {
+      F[i] = 0.0;
+      for (int j = 0; j < 16; ++j) F[i] += part[j][i];
     }
     const double sa = ((F[1] + F[2]) + (F[3] + F[4])) + (F[5] + F[6]);
     const double sd = ((F[7] + F[8]) + (F[9] + F[10])) + ((F[11] + F[12]) + (F[13] + F[14]));
@@ -318,7 +333,8 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense,
 
 cudaError_t launch_conserved(int prec, const void* f, const Layout& L, const Model<double>& m, double* partials,
                              int max_blocks, unsigned* counter, double* result, unsigned* flags, cudaStream_t st) {
-  int b = blocks_for(L.ncell(), RED_THREADS);
+  // about four rows per warp, at most max_blocks blocks
+  int b = blocks_for((long long)L.ny * L.nz, 4 * (RED_THREADS / 32));
   if (b > max_blocks) b = max_blocks;
   if (b < 1) b = 1;
   if (prec == LBM_FP64)

@@ -29,7 +29,6 @@ using ring::mbar_init;
 using ring::mbar_expect_tx;
 using ring::mbar_wait;
 using ring::tma_load_plane;
-using ring::tma_prefetch_plane;
 
 // Tile geometry of the pair kernel: a TX x TY column of cells, 128 threads
 // each owning the cell pair (x, x+1), and an NSLOT-plane ring holding planes
@@ -75,6 +74,30 @@ __device__ __forceinline__ int wrapi(int k, int n) {
   return r < 0 ? r + n : r;
 }
 
+// rho, u, T of one cell from its 15 values (stride pl floats) in FP64
+// (relations e1-e3 summed in double); out of line, called only for cells
+// whose FP32 recovery is ill-conditioned (RecoverDesc).
+struct Macro1 {
+  float rho, ux, uy, uz, T;
+};
+__device__ __noinline__ Macro1 recover_fp64(const float* q, int pl, double c1, double s, double eta0sq,
+                                            double c1sq, double c2sq, double inv_b) {
+  double f[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) f[i] = (double)q[i * pl];
+  const double sa = ((f[1] + f[2]) + (f[3] + f[4])) + (f[5] + f[6]);
+  const double dpp = f[7] + f[8], dpm = f[9] + f[10], dmp = f[11] + f[12], dmm = f[13] + f[14];
+  const double sd = (dpp + dpm) + (dmp + dmm);
+  const double rho = f[0] + sa + sd;
+  const double mx = c1 * (f[1] - f[2]) + s * ((dpp + dpm) - (dmp + dmm));
+  const double my = c1 * (f[3] - f[4]) + s * ((dpp + dmp) - (dpm + dmm));
+  const double mz = c1 * (f[5] - f[6]) + s * (((f[7] + f[9]) + (f[11] + f[13])) - ((f[8] + f[10]) + (f[12] + f[14])));
+  const double E = eta0sq * f[0] + c1sq * sa + c2sq * sd;
+  const double ux = mx / rho, uy = my / rho, uz = mz / rho;
+  const double T = (E / rho - (ux * ux + uy * uy + uz * uz)) * inv_b;
+  return {(float)rho, (float)ux, (float)uy, (float)uz, (float)T};
+}
+
 // The two layers outside an x face from the boundary cell c0 (next to the
 // face) and its neighbour c1 (Sec. 4(2)): g1 next to the face, g2 outside it.
 __device__ __forceinline__ void x_face_layers(const Model<float>& m, int kind, const float c0[NV], const float c1[NV],
@@ -106,7 +129,8 @@ __device__ __forceinline__ void x_face_layers(const Model<float>& m, int kind, c
 template <int SCHEME, bool WT, class G>
 __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* __restrict__ fin,
                                           float* __restrict__ fout, const Layout& L, const Model<float>& m,
-                                          const WtDesc& wt, int x0, int y0, int z0, int nzc,
+                                          const WtDesc& wt, const RecoverDesc& rd, int x0, int y0, int z0,
+                                          int nzc,
                                           unsigned* __restrict__ flags, unsigned char* smem, uint64_t* bars,
                                           unsigned& jb, bool& timed_out, unsigned wait_limit) {
   constexpr int NSLOT = G::NSLOT, PL = G::PL, BX = G::BX;
@@ -119,15 +143,14 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   // z0 .. z0+nzc+1); cell plane k reads ring planes k, k+1, k+2
   const int nplanes = nzc + 2;
 
-  // plane j (interior z0 + j, padded z0 + j + 2); the plane two issues ahead
-  // is prefetched into L2 at the same time
+  // copy ring plane j (interior z0 + j, padded z0 + j + 2) into its slot; an
+  // added L2 prefetch two planes ahead measured 2.5% slower on 256^3
   int issued = 0;  // thread 0 only
   auto issue = [&](int j) {
     const unsigned g = jb + (unsigned)j;
     float* dst = reinterpret_cast<float*>(smem + (g % NSLOT) * G::SLOT_STRIDE);
     mbar_expect_tx(&bars[g % NSLOT], G::SLOT_BYTES);
     tma_load_plane(dst, tin, x0 + OX - 2, y0, z0 + j + 2, &bars[g % NSLOT]);
-    if (j + 2 < nplanes) tma_prefetch_plane(tin, x0 + OX - 2, y0, z0 + j + 4);
     issued = j + 1;
   };
   if (tid == 0) {
@@ -191,7 +214,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     const float2 sa = add(add(add(F[1], F[2]), add(F[3], F[4])), add(F[5], F[6]));
     const float2 dpp = add(F[7], F[8]), dpm = add(F[9], F[10]), dmp = add(F[11], F[12]), dmm = add(F[13], F[14]);
     const float2 sd = add(add(dpp, dpm), add(dmp, dmm));
-    const float2 rho = add(add(F[0], sa), sd);
+    float2 rho = add(add(F[0], sa), sd);
     const float2 mx = fma2(bc2(m.c1), sub(F[1], F[2]), mul(bc2(m.s), sub(add(dpp, dpm), add(dmp, dmm))));
     const float2 my = fma2(bc2(m.c1), sub(F[3], F[4]), mul(bc2(m.s), sub(add(dpp, dmp), add(dpm, dmm))));
     const float2 mz = fma2(bc2(m.c1), sub(F[5], F[6]),
@@ -199,9 +222,31 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
                                              add(add(F[8], F[10]), add(F[12], F[14])))));
     const float2 E = fma2(bc2(m.eta0sq), F[0], fma2(bc2(m.c1sq), sa, mul(bc2(m.c2sq), sd)));
     const float2 ir = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
-    const float2 ux = mul(mx, ir), uy = mul(my, ir), uz = mul(mz, ir);
-    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul(uz, uz)));
-    const float2 T = mul(sub(mul(E, ir), usq), bc2(m.inv_b));
+    float2 ux = mul(mx, ir), uy = mul(my, ir), uz = mul(mz, ir);
+    float2 usq = fma2(ux, ux, fma2(uy, uy, mul(uz, uz)));
+    float2 T = mul(sub(mul(E, ir), usq), bc2(m.inv_b));
+    if (rd.on) {
+      // ill-conditioned FP32 temperature (RecoverDesc): redo the cell in FP64
+      const float2 Aa = fma2(bc2(m.AaT), T, fma2(bc2(m.AaU), usq, bc2(m.Aa0)));
+      const float2 Ad = fma2(bc2(m.AdT), T, fma2(bc2(m.AdU), usq, bc2(m.Ad0)));
+      const float lhs0 = fmaf(rd.axis_w, fabsf(Aa.x), fmaf(rd.diag_w, fabsf(Ad.x), usq.x));
+      const float lhs1 = fmaf(rd.axis_w, fabsf(Aa.y), fmaf(rd.diag_w, fabsf(Ad.y), usq.y));
+      const bool need0 = act0 && !(lhs0 <= rd.thresh_b * T.x);
+      const bool need1 = act1 && !(lhs1 <= rd.thresh_b * T.y);
+      if (need0 || need1) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          if (!(h == 0 ? need0 : need1)) continue;
+          const Macro1 r = recover_fp64(P0 + c + h, PL, rd.c1, rd.s, rd.eta0sq, rd.c1sq, rd.c2sq, rd.inv_b);
+          if (h == 0) {
+            rho.x = r.rho; ux.x = r.ux; uy.x = r.uy; uz.x = r.uz; T.x = r.T;
+          } else {
+            rho.y = r.rho; ux.y = r.ux; uy.y = r.uy; uz.y = r.uz; T.y = r.T;
+          }
+        }
+        usq = fma2(ux, ux, fma2(uy, uy, mul(uz, uz)));
+      }
+    }
     {
       const float ax[2] = {rho.x, rho.y}, tt[2] = {T.x, T.y};
       const float chk[2] = {fabsf(rho.x) + fabsf(T.x) + fabsf(ux.x) + fabsf(uy.x) + fabsf(uz.x),
@@ -451,7 +496,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
 template <int SCHEME, bool WT, class G>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_kernel(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
-                     Layout L, Model<float> m, WtDesc wt, int zc, unsigned* __restrict__ flags,
+                     Layout L, Model<float> m, WtDesc wt, RecoverDesc rd, int zc, unsigned* __restrict__ flags,
                      unsigned wait_limit) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSLOT * G::SLOT_STRIDE);
@@ -464,13 +509,16 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   const int z0 = blockIdx.z * zc;
   unsigned jb = 0;
   bool timed_out = false;
-  pair_unit<SCHEME, WT, G>(&tin, fin, fout, L, m, wt, blockIdx.x * G::TX, blockIdx.y * G::TY, z0,
+  pair_unit<SCHEME, WT, G>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY, z0,
                            min(zc, L.nz - z0), flags, smem, bars, jb, timed_out, wait_limit);
 }
 
-// Persistent batched step: the CTAs walk the units of every grid in the
-// descriptor table (grid-major, then z chunk, then tile), each unit being one
-// z-march of a TX x TY column of one grid.
+// Persistent batched step: two CTAs per SM take the units of every grid in
+// the descriptor table (grid-major, then z chunk, then tile; each unit one
+// z-march of a TX x TY column of one grid) from a work queue, one atomic
+// increment per unit, so fast and slow CTAs balance.  Every CTA overshoots
+// the queue once; the last CTA to finish resets the queue for the next
+// launch (stream order), which keeps the launch replayable in a CUDA graph.
 template <int SCHEME, class G>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_batch_kernel(const __grid_constant__ BatchTable tab) {
@@ -484,7 +532,13 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   __syncthreads();
   unsigned jb = 0;
   bool timed_out = false;
-  for (long long u = blockIdx.x; u < tab.total_units && !timed_out; u += gridDim.x) {
+  __shared__ long long next;
+  for (;;) {
+    if (threadIdx.x == 0) next = (long long)atomicAdd(tab.queue, 1ull);
+    __syncthreads();
+    const long long u = next;
+    __syncthreads();
+    if (u >= tab.total_units || timed_out) break;
     int e = 0;
     while (e + 1 < tab.n && u >= tab.item[e + 1].first_unit) ++e;
     const BatchItem& it = tab.item[e];
@@ -493,9 +547,17 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     const int chunk = (int)(local / per_chunk);
     const int t = (int)(local % per_chunk);
     const int z0 = chunk * it.zc;
-    pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, it.L, it.m, it.wt, (t % it.tiles_x) * G::TX,
+    pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, it.L, it.m, it.wt, it.rd, (t % it.tiles_x) * G::TX,
                                (t / it.tiles_x) * G::TY, z0, min(it.zc, it.L.nz - z0), it.flags, smem, bars, jb,
                                timed_out, tab.wait_limit);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(tab.done, 1u) == gridDim.x - 1) {
+      *tab.queue = 0ull;
+      *tab.done = 0u;
+      __threadfence();
+    }
   }
 }
 
@@ -514,28 +576,28 @@ cudaError_t set_attributes() {
 
 template <int SCHEME, class G>
 cudaError_t launch_scheme(const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                          const Model<float>& m, const WtDesc& wt, int zc, unsigned* flags, unsigned wait_limit,
-                          cudaStream_t st) {
+                          const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
+                          unsigned wait_limit, cudaStream_t st) {
   dim3 grid((L.nx + G::TX - 1) / G::TX, (L.ny + G::TY - 1) / G::TY, (L.nz + zc - 1) / zc);
   const bool any = wt.per[0] || wt.per[1] || wt.per[2] || wt.xlo || wt.xhi;
   if (any)
-    step_pair_kernel<SCHEME, true, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, zc, flags,
+    step_pair_kernel<SCHEME, true, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zc, flags,
                                                                          wait_limit);
   else
-    step_pair_kernel<SCHEME, false, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, zc, flags,
+    step_pair_kernel<SCHEME, false, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zc, flags,
                                                                           wait_limit);
   return cudaGetLastError();
 }
 
 template <class G>
 cudaError_t launch_geo(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                       const Model<float>& m, const WtDesc& wt, int zc, unsigned* flags, unsigned wait_limit,
-                       cudaStream_t st) {
+                       const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
+                       unsigned wait_limit, cudaStream_t st) {
   switch (scheme) {
-    case LBM_SCHEME_NND: return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, zc, flags, wait_limit, st);
+    case LBM_SCHEME_NND: return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
     case LBM_SCHEME_UPWIND2:
-      return launch_scheme<LBM_SCHEME_UPWIND2, G>(map, fin, fout, L, m, wt, zc, flags, wait_limit, st);
-    default: return launch_scheme<LBM_SCHEME_UPWIND1, G>(map, fin, fout, L, m, wt, zc, flags, wait_limit, st);
+      return launch_scheme<LBM_SCHEME_UPWIND2, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+    default: return launch_scheme<LBM_SCHEME_UPWIND1, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
   }
 }
 
@@ -565,9 +627,9 @@ cudaError_t launch_step_pair_batch(int scheme, const BatchTable& tab, int grid, 
 }
 
 cudaError_t launch_step_pair(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                             const Model<float>& m, const WtDesc& wt, int zc, unsigned* flags, unsigned wait_limit,
-                             cudaStream_t st) {
-  return launch_geo<Geo>(scheme, map, fin, fout, L, m, wt, zc, flags, wait_limit, st);
+                             const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
+                             unsigned wait_limit, cudaStream_t st) {
+  return launch_geo<Geo>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
 }
 
 }  // namespace lbm

@@ -17,6 +17,7 @@ constexpr size_t kAlign = 256;
 constexpr int kMaxRedBlocks = 2048;
 constexpr size_t kRedBytes = (size_t)kMaxRedBlocks * 16 * sizeof(double);  // 15 field totals per block
 constexpr size_t kStatusBytes = 256;
+constexpr double kDefaultKappaMax = 0.0;  // FP64 temperature recovery threshold (0 = off)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -49,6 +50,22 @@ Layout make_layout(const lbm_grid* g) {
 size_t field_bytes(const Layout& L, int esz) { return align_up((size_t)lbm::NV * (size_t)L.fs * esz, kAlign); }
 
 // Coefficients of Eq. "eq" regrouped per shell as affine functions of T and u^2.
+// FP64 temperature recovery for cells with kappa > kappa_max (0 = off).
+lbm::RecoverDesc make_recover(const Model<double>& m, double kappa_max) {
+  lbm::RecoverDesc r;
+  r.c1 = m.c1;
+  r.s = m.s;
+  r.eta0sq = m.eta0sq;
+  r.c1sq = m.c1sq;
+  r.c2sq = m.c2sq;
+  r.inv_b = m.inv_b;
+  r.axis_w = (float)(6.0 * m.c1sq);
+  r.diag_w = (float)(8.0 * m.c2sq);
+  r.on = kappa_max > 0.0;
+  r.thresh_b = r.on ? (float)((kappa_max - 1.0) / m.inv_b) : 0.0f;
+  return r;
+}
+
 Model<double> make_model(const lbm_vset* v, double tau, double dt, double dx, int dissipation) {
   Model<double> m;
   const double c1 = v->c1, c2 = v->c2, e0 = v->eta0;
@@ -123,6 +140,8 @@ struct lbm_sim {
   double* partials;
   unsigned* flags;
   unsigned* counter;
+  unsigned long long* queue;  // batched-step work queue (status block)
+  unsigned* done;
   double* result;
   cudaStream_t st;
   int64_t steps;
@@ -134,6 +153,7 @@ struct lbm_sim {
   int zchunk;           // 0 = automatic
   int num_sms;
   CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers (box 36 x 12 x 1 x 15)
+  lbm::RecoverDesc rd;  // FP64 temperature recovery of the pair kernel
   // launch counting and event-pair timing
   int64_t launches[LBM_NKERNEL];
   double ms[LBM_NKERNEL];
@@ -258,15 +278,18 @@ bool make_tmap(CUtensorMap* map, void* base, const Layout& L, int bx, int by) {
 // Variants whose step kernel writes the boundary layers of its output.
 bool wt_variant(int variant) { return variant == LBM_VARIANT_TILED; }
 
-// z planes per CTA of the tiled kernels: about four waves of two CTAs per SM.
+// z planes per CTA of the tiled kernels.  Each unit re-reads four planes
+// around its chunk, so long chunks save traffic; short chunks fill the SMs.
+// On 256^3 (GB300) 16 planes measured best (0.519 ms; 8: 0.540, 32: 0.529,
+// 52: 0.597): the largest of 16, 12, 8, 6, 4 that still gives two waves of
+// two CTAs per SM.  The autotuner (autotune.py) refines this per grid.
 int auto_zchunk(const Layout& L, int num_sms) {
   const long long tiles = (long long)((L.nx + lbm::kTileX - 1) / lbm::kTileX) * ((L.ny + lbm::kTileY - 1) / lbm::kTileY);
-  const long long want = 4LL * 2 * num_sms;
-  long long chunks = (want + tiles - 1) / tiles;
-  long long maxc = L.nz / 8 > 0 ? L.nz / 8 : 1;
-  if (chunks > maxc) chunks = maxc;
-  if (chunks < 1) chunks = 1;
-  return (int)((L.nz + chunks - 1) / chunks);
+  const long long want = 2LL * 2 * num_sms;
+  static const int cand[] = {16, 12, 8, 6, 4};
+  for (int zc : cand)
+    if (tiles * ((L.nz + zc - 1) / zc) >= want) return zc < L.nz ? zc : L.nz;
+  return L.nz < 4 ? L.nz : 4;
 }
 
 unsigned step_faces(const lbm_sim* s) {
@@ -369,6 +392,7 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
   s->dissipation = 1;
   s->md = make_model(vset, tau, dt, dx, 1);
   s->mf = to_float(s->md);
+  s->rd = make_recover(s->md, kDefaultKappaMax);
   for (int a = 0; a < 3; ++a) {
     s->bc.kind[2 * a] = grid->bc_lo[a];
     s->bc.kind[2 * a + 1] = grid->bc_hi[a];
@@ -386,6 +410,8 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
   char* status = s->ws + 2 * fb + kRedBytes;
   s->flags = (unsigned*)status;
   s->counter = (unsigned*)(status + 4);
+  s->queue = (unsigned long long*)(status + 16);
+  s->done = (unsigned*)(status + 24);
   s->result = (double*)(status + 64);
   s->cur = 0;
   s->st = (cudaStream_t)cuda_stream;
@@ -448,6 +474,14 @@ int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk) {
   return LBM_OK;
 }
 
+int lbm_set_t_recovery(lbm_sim* s, double kappa_max) {
+  if (!s) return LBM_EINVAL;
+  if (s->failed) return LBM_ESTATE;
+  if (!(kappa_max == 0.0 || kappa_max >= 1.0)) return LBM_EINVAL;
+  s->rd = make_recover(s->md, kappa_max);
+  return LBM_OK;
+}
+
 int lbm_set_wait_limit(lbm_sim* s, uint32_t polls) {
   if (!s) return LBM_EINVAL;
   if (s->failed) return LBM_ESTATE;
@@ -504,7 +538,7 @@ int run_steps(lbm_sim* s, int64_t n) {
       if (pair) {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_pair(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf, wt,
-                                         zc, s->flags, s->wait_limit, s->st));
+                                         s->rd, zc, s->flags, s->wait_limit, s->st));
       } else {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf,
@@ -521,7 +555,7 @@ int run_steps(lbm_sim* s, int64_t n) {
   return LBM_OK;
 }
 
-constexpr int kBatchZchunk = 32;
+constexpr int kBatchZchunk = 16;  // measured: 16 planes 0.527 ms, 32 planes 0.536 ms on 256^3
 
 int batch_check(lbm_sim* const* sims, int32_t n) {
   if (!sims || n < 1 || n > lbm::kMaxBatch) return LBM_EINVAL;
@@ -566,6 +600,7 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
       it.L = s->L;
       it.m = s->mf;
       it.wt = wt[i];
+      it.rd = s->rd;
       it.tiles_x = (s->L.nx + lbm::kTileX - 1) / lbm::kTileX;
       it.tiles_y = (s->L.ny + lbm::kTileY - 1) / lbm::kTileY;
       it.zc = s->zchunk > 0 ? s->zchunk : kBatchZchunk;
@@ -575,6 +610,8 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
     tab.n = n;
     tab.wait_limit = s0->wait_limit;
     tab.total_units = units;
+    tab.queue = s0->queue;
+    tab.done = s0->done;
     const long long resident = 2LL * s0->num_sms;  // two CTAs per SM
     const int grid = (int)(units < resident ? units : resident);
     LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(s0->scheme, tab, grid, s0->st));

@@ -58,6 +58,23 @@ struct Model {
   R keep0, keep1, keep2;
 };
 
+// FP64 temperature recovery of the FP32 pair kernel.  T = (E/rho - u^2)/b
+// with E = eta0^2 f_0 + c1^2 sum_axis f + c2^2 sum_diag f: when c1^2 >> T the
+// equilibrium's axis and diagonal populations are large and of opposite sign,
+// and E is a small difference of large terms (Sec. 2's A_i of the two shells).
+// At f ~ f^eq the terms sum in magnitude to about rho (6 c1^2 |A_a| +
+// 8 c2^2 |A_d| + (b-3) T) + rho u^2, so the relative rounding error of an FP32
+// T is about eps_32 kappa with
+//   kappa = 1 + (6 c1^2 |A_a| + 8 c2^2 |A_d| + u^2) / (b T).
+// Cells with kappa > kappa_max (or T <= 0 in FP32) recompute rho, u and T from
+// their 15 values in FP64.
+struct RecoverDesc {
+  double c1, s, eta0sq, c1sq, c2sq, inv_b;  // moment constants in FP64
+  float axis_w, diag_w;                     // 6 c1^2, 8 c2^2
+  float thresh_b;                           // (kappa_max - 1) b
+  int on;                                   // 0: FP32 recovery everywhere
+};
+
 struct BcDesc {
   int kind[6];          // face 2a+hi: LBM_BC_*
   double fixed[6][5];   // (rho,u1,u2,u3,T)
@@ -192,8 +209,8 @@ cudaError_t launch_step_tiled(int scheme, const CUtensorMap& map, const float* f
 // Pair kernel: the tiles and TMA box of the tiled kernel (kTileX x kTileY,
 // box tiled_box_x() x tiled_box_y()), two cells per thread.
 cudaError_t launch_step_pair(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                             const Model<float>& m, const WtDesc& wt, int zc, unsigned* flags, unsigned wait_limit,
-                             cudaStream_t st);
+                             const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
+                             unsigned wait_limit, cudaStream_t st);
 
 // Descriptor table of a batched step (passed by value as the kernel
 // parameter): one entry per grid, units [first_unit, first_unit +
@@ -206,6 +223,7 @@ struct BatchItem {
   Layout L;
   Model<float> m;
   WtDesc wt;
+  RecoverDesc rd;
   int tiles_x, tiles_y, zc;
   long long first_unit;
 };
@@ -215,6 +233,8 @@ struct BatchTable {
   int n;
   unsigned wait_limit;
   long long total_units;
+  unsigned long long* queue;  // next unit to take (0 at launch; reset by the last CTA)
+  unsigned* done;             // CTAs finished (0 at launch; reset by the last CTA)
 };
 // Batched step over the descriptor table (same tiles and box).
 cudaError_t launch_step_pair_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st);

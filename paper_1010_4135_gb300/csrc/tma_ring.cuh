@@ -63,14 +63,5 @@ __device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* ma
       : "memory");
 }
 
-// Ask the TMA unit to bring a plane tile into L2 ahead of its shared-memory
-// copy (no shared memory, no completion to wait for).
-__device__ __forceinline__ void tma_prefetch_plane(const CUtensorMap* map, int x, int y, int z) {
-  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y), "r"(z), "r"(0)
-               : "memory");
-}
-
 }  // namespace ring
 }  // namespace lbm

@@ -21,6 +21,7 @@ import torch
 
 import workloads
 from . import _abi as A
+from . import autotune
 from . import sim as S
 from . import stability
 
@@ -59,9 +60,10 @@ def workspace_bytes(grid, precision=A.LBM_FP32) -> int:
 class Server:
     """hbm_budget: bytes of workspace the resident grids may hold together
     (default: 80% of the device's free memory); tick: most steps launched
-    between two retirement checks."""
+    between two retirement checks; tune: give each admitted grid the z chunk
+    the autotuner measured for its shape (once per shape, then cached)."""
 
-    def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False):
+    def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False, tune=True):
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(0.8 * free)
@@ -69,6 +71,7 @@ class Server:
         self.max_batch = int(max_batch)
         self.tick = int(tick)
         self.keep_results = keep_results
+        self.tune = tune
         self.peak_bytes = 0
         self.peak_batch = 0
         self.launches = 0
@@ -78,6 +81,8 @@ class Server:
         s = S.from_workload(w, precision="fp32")
         rho, u, T = w.initial_fields()
         s.init(rho, u, T)
+        if self.tune:
+            autotune.tune(s)
         job.sim = s
         job.remaining = job.req["steps"]
 

@@ -33,6 +33,11 @@ class Sim:
                  dissipation=True, device=None, stream=None, workspace=None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_1010_4135_gb300.Sim needs a CUDA device (GB300)")
+        # constructor arguments, for clone() (the launch configuration is set separately)
+        self._config = dict(nx=nx, ny=ny, nz=nz, c1=c1, c2=c2, eta0=eta0, tau=tau, dt=dt, dx=dx, gamma=gamma,
+                            precision=precision, bc_lo=bc_lo, bc_hi=bc_hi, fixed_lo=fixed_lo, fixed_hi=fixed_hi,
+                            scheme=scheme, dissipation=dissipation, device=device)
+        self.launch = ("tiled", 0)
         self.shape = (int(nz), int(ny), int(nx))
         self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.dtype = np.float64 if self.prec == A.LBM_FP64 else np.float32
@@ -58,7 +63,16 @@ class Sim:
         if scheme != "nnd" or not dissipation:
             self.set_scheme(scheme, dissipation)
 
+    @property
+    def config(self) -> dict:
+        return dict(self._config)
+
     # -- lifetime -------------------------------------------------------------
+    def clone(self, stream=None) -> "Sim":
+        """A new sim of the same grid, constants, boundaries and scheme (own
+        workspace; state undefined until init / set_f)."""
+        return Sim(**self._config, stream=stream)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             A.lbm_destroy(self._h)
@@ -79,6 +93,12 @@ class Sim:
         return self.shape[0] * self.shape[1] * self.shape[2]
 
     # -- state ----------------------------------------------------------------
+    def set_t_recovery(self, kappa_max: float):
+        """FP64 temperature recovery of the FP32 tiled step for cells whose FP32
+        T is ill-conditioned (kappa > kappa_max; 0 = off); see lbm_set_t_recovery."""
+        A.check(A.lbm_set_t_recovery(self._h, float(kappa_max)), "lbm_set_t_recovery")
+        self.t_recovery = float(kappa_max)
+
     def set_scheme(self, scheme="nnd", dissipation=True):
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         A.check(A.lbm_set_scheme(self._h, s, int(bool(dissipation))), "lbm_set_scheme")
@@ -91,6 +111,7 @@ class Sim:
              "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL}[variant] \
             if isinstance(variant, str) else int(variant)
         A.check(A.lbm_set_launch(self._h, v, int(zchunk)), "lbm_set_launch")
+        self.launch = (variant, int(zchunk))
 
     def init(self, rho, u, T):
         """f = f^eq(rho, u, T); arrays shaped [nz,ny,nx] / [3,nz,ny,nx] (numpy or CUDA tensors)."""

@@ -78,27 +78,47 @@ def cell_centres(n: int, dx: float) -> np.ndarray:
     return (np.arange(n, dtype=np.float64) + 0.5) * dx
 
 
-def _two_state_x(w: Workload, left, right, x0: float):
-    x = cell_centres(w.nx, w.dx)
-    L = np.asarray(left, dtype=np.float64)
-    R = np.asarray(right, dtype=np.float64)
-    sel = (x < x0)[None, None, :]
-    shape = (w.nz, w.ny, w.nx)
-    rho = np.where(sel, L[0], R[0]) * np.ones(shape)
-    u = np.stack([np.where(sel, L[1 + a], R[1 + a]) * np.ones(shape) for a in range(3)])
-    T = np.where(sel, L[4], R[4]) * np.ones(shape)
+def _blend(weight, a, b):
+    """Fields of state a where weight = 1 and b where weight = 0, blended in
+    (rho, u, p) so that a pressure-matched interface keeps its pressure."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+
+    def pick(va, vb, mixed):  # exact end states where the weight is 0 or 1
+        return np.where(weight == 1.0, va, np.where(weight == 0.0, vb, mixed))
+
+    rho_m = b[0] + weight * (a[0] - b[0])
+    p_m = b[0] * b[4] + weight * (a[0] * a[4] - b[0] * b[4])
+    rho = pick(a[0], b[0], rho_m)
+    u = np.stack([pick(a[1 + k], b[1 + k], b[1 + k] + weight * (a[1 + k] - b[1 + k])) for k in range(3)])
+    T = pick(a[4], b[4], p_m / rho_m)
     return rho, u, T
 
 
-def shock_tube(name, nx, ny, nz, dx, left, right, x0, c1, c2, eta0, dt, tau, steps, gamma=GAMMA):
+def interface_weight(dist, width: float, dx: float):
+    """1 on the inside (dist < 0) and 0 outside: a sharp step (the cell
+    centre decides) when width = 0, else 0.5 (1 - tanh(dist / (width dx)))."""
+    if width <= 0:
+        return (dist < 0).astype(np.float64)
+    return 0.5 * (1.0 - np.tanh(dist / (width * dx)))
+
+
+def _two_state_x(w: Workload, left, right, x0: float):
+    x = cell_centres(w.nx, w.dx)
+    wt = interface_weight(x - x0, w.meta.get("width", 0.0), w.dx)[None, None, :] * np.ones((w.nz, w.ny, w.nx))
+    return _blend(wt, left, right)
+
+
+def shock_tube(name, nx, ny, nz, dx, left, right, x0, c1, c2, eta0, dt, tau, steps, gamma=GAMMA, width=0.0):
     """Riemann problem along x, periodic in y and z, x faces held at the
-    initial left/right states (no wave reaches them before the end time)."""
+    initial left/right states (no wave reaches them before the end time).
+    width: interface thickness in cells (0 = sharp, see interface_weight)."""
     w = Workload(name=name, nx=nx, ny=ny, nz=nz, dx=dx, c1=c1, c2=c2, eta0=eta0, dt=dt, tau=tau,
                  steps=steps, gamma=gamma,
                  bc_lo=(FIXED, PERIODIC, PERIODIC), bc_hi=(FIXED, PERIODIC, PERIODIC),
                  fixed_lo=(tuple(left), (0.0,) * 5, (0.0,) * 5),
                  fixed_hi=(tuple(right), (0.0,) * 5, (0.0,) * 5),
-                 meta={"left": tuple(left), "right": tuple(right), "x0": x0})
+                 meta={"left": tuple(left), "right": tuple(right), "x0": x0, "width": float(width)})
     w.ic = _tube_ic
     return w
 
@@ -108,30 +128,29 @@ def _tube_ic(w: Workload):
 
 
 def _sphere_ic(w: Workload):
-    amb = np.asarray(w.meta["ambient"], dtype=np.float64)
-    sph = np.asarray(w.meta["sphere"], dtype=np.float64)
     cx, cy, cz = w.meta["centre"]
     R = w.meta["radius"]
     x = cell_centres(w.nx, w.dx)
     y = cell_centres(w.ny, w.dx)
     z = cell_centres(w.nz, w.dx)
-    r2 = (x[None, None, :] - cx) ** 2 + (y[None, :, None] - cy) ** 2 + (z[:, None, None] - cz) ** 2
-    inside = r2 <= R * R
-    shape = (w.nz, w.ny, w.nx)
-    rho = np.where(inside, sph[0], amb[0]) * np.ones(shape)
-    u = np.stack([np.where(inside, sph[1 + a], amb[1 + a]) * np.ones(shape) for a in range(3)])
-    T = np.where(inside, sph[4], amb[4]) * np.ones(shape)
-    return rho, u, T
+    r = np.sqrt((x[None, None, :] - cx) ** 2 + (y[None, :, None] - cy) ** 2 + (z[:, None, None] - cz) ** 2)
+    width = w.meta.get("width", 0.0)
+    if width <= 0:
+        wt = (r * r <= R * R).astype(np.float64)  # the cell centre decides, r = R inside
+    else:
+        wt = interface_weight(r - R, width, w.dx)
+    return _blend(wt, w.meta["sphere"], w.meta["ambient"])
 
 
 def shock_sphere(name, nx, ny, nz, dx, mach, sphere_rho, radius, centre, c1, c2, eta0, dt, tau, steps,
-                 ambient_rho=1.0, ambient_p=1.0, gamma=GAMMA):
+                 ambient_rho=1.0, ambient_p=1.0, gamma=GAMMA, width=1.0):
     """Planar shock entering at x = 0 into gas at rest holding a sphere of
     another density at the same pressure.  The domain starts all pre-shock;
     the x-lo boundary layers hold the post-shock state, so the boundary
     Riemann problem is exactly the shock of the given Mach number.  x-hi
-    extrapolates, y and z are periodic.  Sphere membership: cell centre
-    within the radius (sharp)."""
+    extrapolates, y and z are periodic.  Sphere surface: a tanh profile
+    `width` cells thick (interface_weight; 0 = sharp, the cell centre
+    decides), blended at constant pressure."""
     rho2, u2, p2, D = rankine_hugoniot(mach, ambient_rho, ambient_p, gamma)
     post = state_from_p(rho2, u2, 0.0, 0.0, p2)
     amb = state_from_p(ambient_rho, 0.0, 0.0, 0.0, ambient_p)
@@ -141,7 +160,7 @@ def shock_sphere(name, nx, ny, nz, dx, mach, sphere_rho, radius, centre, c1, c2,
                  bc_lo=(FIXED, PERIODIC, PERIODIC), bc_hi=(EXTRAPOLATE, PERIODIC, PERIODIC),
                  fixed_lo=(post, (0.0,) * 5, (0.0,) * 5),
                  meta={"ambient": amb, "sphere": sph, "post": post, "centre": tuple(centre),
-                       "radius": radius, "mach": mach, "shock_speed": D})
+                       "radius": radius, "mach": mach, "shock_speed": D, "width": float(width)})
     w.ic = _sphere_ic
     return w
 
@@ -260,13 +279,14 @@ def request_workload(req, c1, c2, eta0, dt):
     """The Workload of a request with the given model constants.  Tube: the
     post-shock state (x < 0.3 of the domain) against gas of the request's
     density ratio; sphere: the shock entering at x = 0 into ambient gas holding
-    a sphere of that density (radius 0.1 L_y, centre (0.3 L_x, 0.5, 0.5))."""
+    a sphere of that density (radius 0.1 L_y, centre (0.3 L_x, 0.5, 0.5)).
+    Both interfaces are one cell thick (interface_weight)."""
     nx, ny, nz = req["grid"]
     dx = 1.0 / ny
     pre, post, other = request_states(req)
     if req["kind"] == "tube":
         w = shock_tube(f"req{req['id']}_tube", nx, ny, nz, dx, post, other, 0.3 * nx * dx, c1, c2, eta0, dt, dt,
-                       req["steps"])
+                       req["steps"], width=1.0)
     else:
         w = shock_sphere(f"req{req['id']}_sphere", nx, ny, nz, dx, req["mach"], req["ratio"], 0.1,
                          (0.3 * nx * dx, 0.5, 0.5), c1, c2, eta0, dt, dt, req["steps"])
