@@ -47,7 +47,7 @@ def parse():
                         "step, replayed as a CUDA graph; serve: the seeded request stream through the "
                         "continuous-batching server")
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
-    p.add_argument("--variant", default="tiled", choices=["tiled", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
+    p.add_argument("--variant", default="tiled", choices=["tiled", "tiled64", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
     p.add_argument("--zchunk", type=int, default=0, help="z planes per CTA of the tiled kernel (0 = auto)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -96,9 +96,12 @@ def run_batch(args):
         sims.append(s)
     cells = sum(w.ncell for w in ws)
     from paper_1010_4135_gb300 import autotune
-    tuned = autotune.tune_batch(sims) if args.zchunk == 0 else {"zchunk": args.zchunk, "cached": None}
+    if args.zchunk == 0:
+        tuned = autotune.tune_batch(sims)
+    else:
+        tuned = {"variant": args.variant if args.variant in ("tiled", "tiled64") else "tiled", "zchunk": args.zchunk}
     for s in sims:
-        s.set_launch("tiled", tuned["zchunk"])
+        s.set_launch(tuned["variant"], tuned["zchunk"])
     S.step_batch(sims, max(2, args.warmup))
     gsteps = 10 if args.steps % 10 == 0 else 2
     steps = max(gsteps, args.steps - args.steps % gsteps)
@@ -130,7 +133,8 @@ def run_batch(args):
         "config": {"workload": "batch: " + ", ".join(w.name for w in ws), "cells": cells,
                    "c1_c2_eta0_dt": [[w.c1, w.c2, w.eta0, w.dt] for w in ws],
                    "launch": f"one persistent batched step kernel per step, CUDA graph of {gsteps} steps",
-                   "zchunk": tuned["zchunk"], "autotuned": args.zchunk == 0, "tune_timings_ms": tuned.get("timings"),
+                   "variant": tuned["variant"], "zchunk": tuned["zchunk"], "autotuned": args.zchunk == 0,
+                   "tune_timings_ms": tuned.get("timings"),
                    "l2": "no flush: 18 f buffers of 1.0-2.0 GB / 0.13 GB exceed the L2"},
         "roofline": {"bound": "hbm", "achieved": alg / per_step / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": alg / per_step / 1e9 / peak, "peak_source": peak_kind,
@@ -341,7 +345,7 @@ def run_ours(args):
     s.set_launch(args.variant, args.zchunk)
     s.init(rho, u, T)
     tuned = None
-    if args.precision == "fp32" and args.variant == "tiled" and args.zchunk == 0:
+    if args.precision == "fp32" and args.variant in ("tiled", "tiled64") and args.zchunk == 0:
         from paper_1010_4135_gb300 import autotune
         tuned = autotune.tune(s)  # z chunk measured on a scratch copy of this state
 
@@ -417,7 +421,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_step_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_kind, "kernel": f"step ({args.precision}, {args.variant if args.precision == 'fp32' else 'plain'})",
+                "peak_source": peak_kind, "kernel": f"step ({args.precision}, {s.launch[0] if args.precision == 'fp32' else 'plain'})",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "traffic": recorded_traffic("step", args.precision, w.ncell),
                 "avg_launch_ms": avg_step_s * 1e3, "fill_avg_launch_ms": fill_ms / max(1, fill_n)}
@@ -434,7 +438,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {**describe(w, args.precision),
-                   "launch": {"variant": args.variant if args.precision == "fp32" else "plain",
+                   "launch": {"variant": s.launch[0] if args.precision == "fp32" else "plain",
                               "zchunk": s.launch[1] if args.precision == "fp32" else None,
                               "autotuned": tuned is not None,
                               "tune_timings_ms": tuned.get("timings") if tuned else None}},

@@ -77,14 +77,22 @@ enum { LBM_SCHEME_NND = 0, LBM_SCHEME_UPWIND2 = 1, LBM_SCHEME_UPWIND1 = 2 };
 enum { LBM_HEALTH_NONFINITE = 1u, LBM_HEALTH_RHO = 2u, LBM_HEALTH_T = 4u, LBM_HEALTH_TIMEOUT = 8u };
 
 /* Step kernel variants of the FP32 path (lbm_set_launch): TILED = TMA plane
- * tiles of 32 x 8 cells, two x-adjacent cells per thread in packed f32x2
- * arithmetic (default); the step kernel also writes the periodic images and
- * the extrapolated / reflected x-face layers of the state it produces, so no
- * fill launch is needed between steps; TILED_FILL = the same kernel with all
- * boundary layers left to a fill launch before each step; TILED_SINGLE = the
- * same tiles, one cell per thread; PLAIN = one thread per cell reading
- * global memory. */
-enum { LBM_VARIANT_TILED = 0, LBM_VARIANT_PLAIN = 1, LBM_VARIANT_TILED_SINGLE = 2, LBM_VARIANT_TILED_FILL = 3 };
+ * tiles of 32 x 8 cells in a four-plane ring (two CTAs of 4 warps per SM),
+ * two x-adjacent cells per thread in packed f32x2 arithmetic (default); the
+ * step kernel also writes the periodic images and the extrapolated /
+ * reflected x-face layers of the state it produces, so no fill launch is
+ * needed between steps; TILED64 = the same on 64 x 8 tiles (one CTA of 8
+ * warps per SM); TILED_FILL = the TILED kernel with all boundary layers left
+ * to a fill launch before each step; TILED_SINGLE = 32 x 8 tiles, one cell
+ * per thread; PLAIN = one thread per cell reading global memory.
+ * lbm_step_batch takes TILED or TILED64 sims (all the same). */
+enum {
+  LBM_VARIANT_TILED = 0,
+  LBM_VARIANT_PLAIN = 1,
+  LBM_VARIANT_TILED_SINGLE = 2,
+  LBM_VARIANT_TILED_FILL = 3,
+  LBM_VARIANT_TILED64 = 4
+};
 
 /* Grid of nx*ny*nz interior cells of edge dx and the boundary kind of each
  * face; fixed_lo/fixed_hi give (rho,u1,u2,u3,T) for FIXED faces (axis 0=x). */

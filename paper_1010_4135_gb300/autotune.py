@@ -1,9 +1,11 @@
 """Launch-configuration autotuner of the FP32 step.
 
-The knob is the z chunk of the tiled pair kernel (planes one CTA marches):
-long chunks re-read fewer boundary planes, short chunks fill the SMs and
-balance the tail.  The best value depends on the grid's shape and the SM
-count, so it is measured: each candidate runs a few steps of the sim's own
+The knobs are the tile shape of the pair kernel ("tiled": 32 x 8 tiles, two
+CTAs of 4 warps per SM; "tiled64": 64 x 8 tiles, one CTA of 8 warps per SM)
+and its z chunk (planes one CTA marches): long chunks
+re-read fewer boundary planes, short chunks fill the SMs and balance the
+tail.  The best pair depends on the grid's shape and the SM count, so it is
+measured: each candidate runs a few steps of the sim's own
 state on a scratch copy of the sim (its own workspace, so the user's state
 and step count are untouched), timed with CUDA events on the scratch sim's
 stream; the fastest is applied and cached per (device, grid, precision,
@@ -20,6 +22,7 @@ import threading
 import torch
 
 ZCHUNKS = (4, 8, 12, 16, 24, 32, 48)
+VARIANTS = ("tiled", "tiled64")
 _lock = threading.Lock()
 
 
@@ -70,8 +73,9 @@ def _time(run, steps: int, warmup: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bool = False) -> dict:
-    """{zchunk: ms per step} of the given sims' current states on scratch copies."""
+def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bool = False,
+            variants=VARIANTS) -> dict:
+    """{(variant, zchunk): ms per step} of the given sims' current states on scratch copies."""
     from . import sim as S
     scratch = []
     try:
@@ -84,45 +88,50 @@ def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bo
                 c = s.clone(stream=torch.cuda.current_stream(s.device))
                 scratch.append((c, f))
             out = {}
-            for zc in zchunks:
-                for c, f in scratch:
-                    c.set_launch("tiled", zc)
-                    c.set_f(f)
-                if batched:
-                    run = lambda n: S.step_batch([c for c, _ in scratch], n)
-                else:
-                    run = scratch[0][0].step
-                out[int(zc)] = _time(run, steps, warmup)
+            for v in variants:
+                for zc in zchunks:
+                    for c, f in scratch:
+                        c.set_launch(v, zc)
+                        c.set_f(f)
+                    if batched:
+                        run = lambda n: S.step_batch([c for c, _ in scratch], n)
+                    else:
+                        run = scratch[0][0].step
+                    out[(v, int(zc))] = _time(run, steps, warmup)
             return out
     finally:
         for c, _ in scratch:
             c.close()
 
 
-def tune(sim, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None) -> dict:
-    """Choose and apply the z chunk of one FP32 sim; returns {"zchunk", "ms", "cached", "timings"}."""
-    return _tune([sim], zchunks, steps, use_cache, path, batched=False)
+def tune(sim, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None,
+         variants=VARIANTS) -> dict:
+    """Choose and apply the tile shape and z chunk of one FP32 sim; returns
+    {"variant", "zchunk", "ms", "cached", "timings"}."""
+    return _tune([sim], zchunks, steps, use_cache, path, batched=False, variants=variants)
 
 
-def tune_batch(sims, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None) -> dict:
-    """Choose and apply one z chunk for sims stepped together (lbm_step_batch)."""
-    return _tune(list(sims), zchunks, steps, use_cache, path, batched=True)
+def tune_batch(sims, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None,
+               variants=VARIANTS) -> dict:
+    """Choose and apply one tile shape and z chunk for sims stepped together (lbm_step_batch)."""
+    return _tune(list(sims), zchunks, steps, use_cache, path, batched=True, variants=variants)
 
 
-def _tune(sims, zchunks, steps, use_cache, path, batched, key=None):
+def _tune(sims, zchunks, steps, use_cache, path, batched, key=None, variants=VARIANTS):
     if any(s.config["precision"] not in ("fp32", 1) for s in sims):
-        return {"zchunk": None, "ms": None, "cached": False, "timings": {}}
+        return {"variant": None, "zchunk": None, "ms": None, "cached": False, "timings": {}}
     path = path or cache_path()
     key = key or key_of(sims, batched)
     hit = _load(path).get(key) if use_cache else None
     if hit is not None:
         for s in sims:
-            s.set_launch("tiled", int(hit["zchunk"]))
+            s.set_launch(hit["variant"], int(hit["zchunk"]))
         return {**hit, "cached": True}
-    timings = measure(sims, zchunks, steps, batched=batched)
+    timings = measure(sims, zchunks, steps, batched=batched, variants=variants)
     best = min(timings, key=timings.get)
     for s in sims:
-        s.set_launch("tiled", best)
-    rec = {"zchunk": best, "ms": timings[best], "timings": {str(k): v for k, v in timings.items()}}
+        s.set_launch(*best)
+    rec = {"variant": best[0], "zchunk": best[1], "ms": timings[best],
+           "timings": {f"{v}:{z}": t for (v, z), t in timings.items()}}
     _store(path, key, rec)
     return {**rec, "cached": False}

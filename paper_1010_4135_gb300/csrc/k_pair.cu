@@ -29,32 +29,45 @@ using ring::mbar_init;
 using ring::mbar_expect_tx;
 using ring::mbar_wait;
 using ring::tma_load_plane;
+using ring::tma_prefetch_plane;
 
-// Tile geometry of the pair kernel: a TX x TY column of cells, 128 threads
-// each owning the cell pair (x, x+1), and an NSLOT-plane ring holding planes
-// z .. z+2 while z+3 lands.
-template <int TX_, int TY_, int NSLOT_>
+// Tile geometry of the pair kernel: a TX x TY column of cells, one thread per
+// cell pair (x, x+1), and a four-plane ring: cell plane z reads ring planes z
+// (its x / y neighbours), z+1 and z+2 while z+3 lands.  PF > 0 also asks the
+// TMA unit to bring ring plane j+PF into L2 when plane j is copied, which
+// keeps more DRAM reads in flight per SM than the ring alone.
+template <int TX_, int TY_, int PF_>
 struct PairGeo {
-  static constexpr int TX = TX_, TY = TY_, NSLOT = NSLOT_;
-  static constexpr int BX = TX + 4, BY = TY + 4;     // tile with a 2-cell halo
-  static constexpr int PL = BX * BY;                 // floats per field in one plane tile
-  static constexpr int SLOT_BYTES = NV * PL * 4;     // bytes one TMA copy delivers
+  static constexpr int TX = TX_, TY = TY_, NSLOT = 4, PF = PF_;
+  static constexpr int BX = TX + 2 * TMA_LEFT, BY = TY + 4;  // tile with its halo
+  static constexpr int PL = BX * BY;                          // floats per field in one plane tile
+  static constexpr int SLOT_BYTES = NV * PL * 4;              // bytes one TMA copy delivers
   static constexpr int SLOT_STRIDE = (SLOT_BYTES + 127) / 128 * 128;
   static constexpr int SMEM = NSLOT * SLOT_STRIDE + NSLOT * 8;
-  static constexpr int PX = TX / 2;                  // threads along x
+  static constexpr int PX = TX / 2;                           // threads along x
   static constexpr int THREADS = PX * TY;
-  static constexpr int CTAS_PER_SM = 2;
-  static_assert(THREADS == 128, "128 threads per CTA");
-  static_assert(PX == 16, "a half warp (one 128-byte shared-memory wavefront of 64-bit loads) is one tile row");
-  static_assert(BX * 4 % 16 == 0, "TMA box inner extent must be a 16-byte multiple");
-  static_assert(TX % 4 == 0, "tile x origin must keep the TMA x coordinate 16-byte aligned");
-  static_assert(NSLOT == 4, "the ring holds planes z .. z+2 and the one landing");
-  static_assert(2 * (SMEM + 1024) <= 233472, "two CTAs per SM");
+  // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved
+  // per CTA, the batched kernel's 8-byte work-queue slot rounded to 128)
+  static constexpr int CTAS_PER_SM = 233472 / (SMEM + 128 + 1024);
+  static_assert(CTAS_PER_SM >= 1, "ring fits one CTA");
+  static_assert(THREADS % 32 == 0, "whole warps");
+  static_assert(PX == 16 || PX == 32,
+                "64-bit shared loads: a half warp (one 128-byte wavefront) reads one contiguous tile row");
+  static_assert(BX * 4 % 16 == 0 && BX <= 256, "TMA box inner extent: a 16-byte multiple, at most 256");
+  static_assert(TX % 32 == 0, "tile rows start on 32-byte sectors (OX is a multiple of 8)");
   __device__ static int col(int tid) { return tid % PX; }
   __device__ static int row(int tid) { return tid / PX; }
 };
-// 32 x 8 tiles: the box (36 x 12 x 1 x 15) is the single-cell tiled kernel's
-using Geo = PairGeo<ring::TX, ring::TY, ring::NSLOT>;
+// 32 x 8 tiles (the single-cell tiled kernel's box, 40 x 12): two CTAs of 4
+// warps per SM, L2 prefetch two planes ahead (256^3: 0.475 ms per step, 0.488
+// without the prefetch).
+using Geo32 = PairGeo<ring::TX, ring::TY, 2>;
+// 64 x 8 tiles (box 72 x 12 x 1 x 15): one CTA of 8 warps per SM, 288-byte
+// row reads.  Its data movement alone (ring + stores, no arithmetic) is
+// faster (0.362 ms against 0.443 ms on 256^3), but with the arithmetic one
+// CTA per SM cannot hide its per-plane barrier: 0.549 ms per step.
+using Geo64 = PairGeo<64, 8, 2>;
+static_assert(Geo32::BX == ring::BX && Geo32::BY == ring::BY, "Geo32 shares the tiled kernel's tensor map");
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -143,14 +156,14 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   // z0 .. z0+nzc+1); cell plane k reads ring planes k, k+1, k+2
   const int nplanes = nzc + 2;
 
-  // copy ring plane j (interior z0 + j, padded z0 + j + 2) into its slot; an
-  // added L2 prefetch two planes ahead measured 2.5% slower on 256^3
+  // copy ring plane j (interior z0 + j, padded z0 + j + 2) into its slot
   int issued = 0;  // thread 0 only
   auto issue = [&](int j) {
     const unsigned g = jb + (unsigned)j;
     float* dst = reinterpret_cast<float*>(smem + (g % NSLOT) * G::SLOT_STRIDE);
     mbar_expect_tx(&bars[g % NSLOT], G::SLOT_BYTES);
-    tma_load_plane(dst, tin, x0 + OX - 2, y0, z0 + j + 2, &bars[g % NSLOT]);
+    tma_load_plane(dst, tin, x0 + OX - TMA_LEFT, y0, z0 + j + 2, &bars[g % NSLOT]);
+    if (G::PF > 0 && j + G::PF < nplanes) tma_prefetch_plane(tin, x0 + OX - TMA_LEFT, y0, z0 + j + G::PF + 2);
     issued = j + 1;
   };
   if (tid == 0) {
@@ -170,7 +183,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     return mbar_wait(&bars[g % NSLOT], (g / NSLOT) & 1u);
   };
 
-  const int c = (ty + 2) * BX + 2 + 2 * tx;  // own pair in a plane tile (even: 8-byte aligned)
+  const int c = (ty + 2) * BX + TMA_LEFT + 2 * tx;  // own pair in a plane tile (even: 8-byte aligned)
   const long long gbase = L.at(x, y, z0);
 
   float2 h1[NV], h2[NV], carry[NV];
@@ -611,25 +624,39 @@ cudaError_t prepare_geo() {
 
 }  // namespace
 
-cudaError_t prepare_pair_kernels() { return prepare_geo<Geo>(); }
+cudaError_t prepare_pair_kernels() {
+  cudaError_t e = prepare_geo<Geo64>();
+  if (e == cudaSuccess) e = prepare_geo<Geo32>();
+  return e;
+}
 
-cudaError_t launch_step_pair_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st) {
+PairShape pair_shape(int cols) {
+  if (cols == 64) return {Geo64::TX, Geo64::TY, Geo64::BX, Geo64::BY, Geo64::THREADS, Geo64::CTAS_PER_SM};
+  return {Geo32::TX, Geo32::TY, Geo32::BX, Geo32::BY, Geo32::THREADS, Geo32::CTAS_PER_SM};
+}
+
+template <class G>
+void launch_batch_geo(int scheme, const BatchTable& tab, int grid, cudaStream_t st) {
   switch (scheme) {
-    case LBM_SCHEME_NND:
-      step_pair_batch_kernel<LBM_SCHEME_NND, Geo><<<grid, Geo::THREADS, Geo::SMEM, st>>>(tab);
-      break;
+    case LBM_SCHEME_NND: step_pair_batch_kernel<LBM_SCHEME_NND, G><<<grid, G::THREADS, G::SMEM, st>>>(tab); break;
     case LBM_SCHEME_UPWIND2:
-      step_pair_batch_kernel<LBM_SCHEME_UPWIND2, Geo><<<grid, Geo::THREADS, Geo::SMEM, st>>>(tab);
+      step_pair_batch_kernel<LBM_SCHEME_UPWIND2, G><<<grid, G::THREADS, G::SMEM, st>>>(tab);
       break;
-    default: step_pair_batch_kernel<LBM_SCHEME_UPWIND1, Geo><<<grid, Geo::THREADS, Geo::SMEM, st>>>(tab);
+    default: step_pair_batch_kernel<LBM_SCHEME_UPWIND1, G><<<grid, G::THREADS, G::SMEM, st>>>(tab);
   }
+}
+
+cudaError_t launch_step_pair_batch(int cols, int scheme, const BatchTable& tab, int grid, cudaStream_t st) {
+  if (cols == 64) launch_batch_geo<Geo64>(scheme, tab, grid, st);
+  else launch_batch_geo<Geo32>(scheme, tab, grid, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_pair(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                             const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
-                             unsigned wait_limit, cudaStream_t st) {
-  return launch_geo<Geo>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+cudaError_t launch_step_pair(int cols, int scheme, const CUtensorMap& map, const float* fin, float* fout,
+                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc,
+                             unsigned* flags, unsigned wait_limit, cudaStream_t st) {
+  if (cols == 64) return launch_geo<Geo64>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+  return launch_geo<Geo32>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
 }
 
 }  // namespace lbm

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(TX* TY, 2)
     const int s = j % NSLOT;
     float* dst = reinterpret_cast<float*>(smem + s * SLOT_STRIDE);
     mbar_expect_tx(&bars[s], SLOT_BYTES_TX);
-    tma_load_plane(dst, &tin, x0 + OX - 2, y0, z0 + j + 2, &bars[s]);
+    tma_load_plane(dst, &tin, x0 + OX - TMA_LEFT, y0, z0 + j + 2, &bars[s]);
     issued = j + 1;
   };
   if (tid == 0) {
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(TX* TY, 2)
     return __syncthreads_or(!ok) == 0;
   };
 
-  const int c = (ty + 2) * BX + (tx + 2);
+  const int c = (ty + 2) * BX + (tx + TMA_LEFT);
   const long long gbase = L.at(x, y, z0);
 
   // own column one and two planes below z0 (ghost planes when z0 = 0)

@@ -152,7 +152,8 @@ struct lbm_sim {
   int variant;          // LBM_VARIANT_* of the FP32 step
   int zchunk;           // 0 = automatic
   int num_sms;
-  CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers (box 36 x 12 x 1 x 15)
+  CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers, box 40 x 12 x 1 x 15 (32 x 8 tiles)
+  CUtensorMap wmap[2];  // the same with box 72 x 12 x 1 x 15 (64 x 8 tiles, variant TILED64)
   lbm::RecoverDesc rd;  // FP64 temperature recovery of the pair kernel
   // launch counting and event-pair timing
   int64_t launches[LBM_NKERNEL];
@@ -276,16 +277,23 @@ bool make_tmap(CUtensorMap* map, void* base, const Layout& L, int bx, int by) {
 }
 
 // Variants whose step kernel writes the boundary layers of its output.
-bool wt_variant(int variant) { return variant == LBM_VARIANT_TILED; }
+bool wt_variant(int variant) { return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED64; }
 
-// z planes per CTA of the tiled kernels.  Each unit re-reads four planes
-// around its chunk, so long chunks save traffic; short chunks fill the SMs.
-// On 256^3 (GB300) 16 planes measured best (0.519 ms; 8: 0.540, 32: 0.529,
-// 52: 0.597): the largest of 16, 12, 8, 6, 4 that still gives two waves of
-// two CTAs per SM.  The autotuner (autotune.py) refines this per grid.
-int auto_zchunk(const Layout& L, int num_sms) {
-  const long long tiles = (long long)((L.nx + lbm::kTileX - 1) / lbm::kTileX) * ((L.ny + lbm::kTileY - 1) / lbm::kTileY);
-  const long long want = 2LL * 2 * num_sms;
+// Variants that run the pair kernel, and its tile width.
+bool pair_variant(int variant) {
+  return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED_FILL || variant == LBM_VARIANT_TILED64;
+}
+int pair_cols(int variant) { return variant == LBM_VARIANT_TILED64 ? 64 : 32; }
+
+// z planes per CTA of the tiled kernels (`cols` x 8 tiles, `ctas` CTAs per
+// SM).  Each unit re-reads four planes around its chunk, so long chunks save
+// traffic; short chunks fill the SMs.  On 256^3 (GB300, 32 x 8 tiles) 16
+// planes measured best (0.519 ms; 8: 0.540, 32: 0.529, 52: 0.597): the
+// largest of 16, 12, 8, 6, 4 that still gives two waves.  The autotuner
+// (autotune.py) refines this per grid.
+int auto_zchunk(const Layout& L, int num_sms, int cols, int ctas) {
+  const long long tiles = (long long)((L.nx + cols - 1) / cols) * ((L.ny + lbm::kTileY - 1) / lbm::kTileY);
+  const long long want = 2LL * ctas * num_sms;
   static const int cand[] = {16, 12, 8, 6, 4};
   for (int zc : cand)
     if (tiles * ((L.nz + zc - 1) / zc) >= want) return zc < L.nz ? zc : L.nz;
@@ -433,8 +441,11 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
     return LBM_ECUDA;
   }
   if (precision == LBM_FP32) {
+    const lbm::PairShape p64 = lbm::pair_shape(64);
     if (!make_tmap(&s->tmap[0], s->fbuf[0], s->L, lbm::tiled_box_x(), lbm::tiled_box_y()) ||
         !make_tmap(&s->tmap[1], s->fbuf[1], s->L, lbm::tiled_box_x(), lbm::tiled_box_y()) ||
+        !make_tmap(&s->wmap[0], s->fbuf[0], s->L, p64.bx, p64.by) ||
+        !make_tmap(&s->wmap[1], s->fbuf[1], s->L, p64.bx, p64.by) ||
         lbm::prepare_tiled_kernels() != cudaSuccess || lbm::prepare_pair_kernels() != cudaSuccess) {
       delete s;
       return LBM_ECUDA;
@@ -467,7 +478,7 @@ int lbm_set_scheme(lbm_sim* s, int32_t scheme, int32_t dissipation) {
 int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk) {
   if (!s) return LBM_EINVAL;
   if (s->failed) return LBM_ESTATE;
-  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED_FILL || zchunk < 0) return LBM_EINVAL;
+  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED64 || zchunk < 0) return LBM_EINVAL;
   s->variant = variant;
   s->zchunk = zchunk;
   s->layers_ok[0] = s->layers_ok[1] = 0;
@@ -522,7 +533,8 @@ int run_steps(lbm_sim* s, int64_t n) {
     int rc = fill_fixed(s);
     if (rc) return rc;
   }
-  const bool pair = s->prec == LBM_FP32 && s->variant != LBM_VARIANT_PLAIN && s->variant != LBM_VARIANT_TILED_SINGLE;
+  const bool pair = s->prec == LBM_FP32 && pair_variant(s->variant);
+  const lbm::PairShape shape = lbm::pair_shape(pair_cols(s->variant));
   unsigned wt_faces = 0;
   const lbm::WtDesc wt = write_through(s, &wt_faces);
   for (int64_t k = 0; k < n; ++k) {
@@ -534,10 +546,13 @@ int run_steps(lbm_sim* s, int64_t n) {
     if (mask)
       LBM_LAUNCH(s, LBM_KERNEL_FILL, lbm::launch_fill(s->prec, fin, s->L, s->md, s->mf, s->bc, mask, s->st));
     if (s->prec == LBM_FP32 && s->variant != LBM_VARIANT_PLAIN) {
-      const int zc = s->zchunk > 0 ? s->zchunk : auto_zchunk(s->L, s->num_sms);
+      const int zc = s->zchunk > 0 ? s->zchunk
+                                   : (pair ? auto_zchunk(s->L, s->num_sms, shape.tx, shape.ctas_per_sm)
+                                           : auto_zchunk(s->L, s->num_sms, lbm::kTileX, 2));
       if (pair) {
+        const CUtensorMap& map = shape.tx == 64 ? s->wmap[s->cur] : s->tmap[s->cur];
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
-                   lbm::launch_step_pair(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf, wt,
+                   lbm::launch_step_pair(shape.tx, s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf, wt,
                                          s->rd, zc, s->flags, s->wait_limit, s->st));
       } else {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
@@ -563,7 +578,7 @@ int batch_check(lbm_sim* const* sims, int32_t n) {
     lbm_sim* s = sims[i];
     if (!s) return LBM_EINVAL;
     if (s->failed) return LBM_ESTATE;
-    if (s->prec != LBM_FP32 || s->variant != LBM_VARIANT_TILED) return LBM_EINVAL;
+    if (s->prec != LBM_FP32 || !wt_variant(s->variant) || s->variant != sims[0]->variant) return LBM_EINVAL;
     if (s->scheme != sims[0]->scheme || s->st != sims[0]->st || s->device != sims[0]->device) return LBM_EINVAL;
     for (int j = 0; j < i; ++j)
       if (sims[j] == s) return LBM_EINVAL;
@@ -575,6 +590,7 @@ int batch_check(lbm_sim* const* sims, int32_t n) {
 // launch of the persistent tile kernel for all sims.
 int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
   lbm_sim* s0 = sims[0];
+  const lbm::PairShape shape = lbm::pair_shape(pair_cols(s0->variant));
   for (int i = 0; i < n; ++i) {
     int rc = fill_fixed(sims[i]);
     if (rc) return rc;
@@ -593,7 +609,7 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
         LBM_LAUNCH(s, LBM_KERNEL_FILL,
                    lbm::launch_fill(s->prec, s->fbuf[s->cur], s->L, s->md, s->mf, s->bc, mask, s->st));
       lbm::BatchItem& it = tab.item[i];
-      tab.map[i] = s->tmap[s->cur];
+      tab.map[i] = shape.tx == 64 ? s->wmap[s->cur] : s->tmap[s->cur];
       it.fin = (const float*)s->fbuf[s->cur];
       it.fout = (float*)s->fbuf[s->cur ^ 1];
       it.flags = s->flags;
@@ -601,8 +617,8 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
       it.m = s->mf;
       it.wt = wt[i];
       it.rd = s->rd;
-      it.tiles_x = (s->L.nx + lbm::kTileX - 1) / lbm::kTileX;
-      it.tiles_y = (s->L.ny + lbm::kTileY - 1) / lbm::kTileY;
+      it.tiles_x = (s->L.nx + shape.tx - 1) / shape.tx;
+      it.tiles_y = (s->L.ny + shape.ty - 1) / shape.ty;
       it.zc = s->zchunk > 0 ? s->zchunk : kBatchZchunk;
       it.first_unit = units;
       units += (long long)it.tiles_x * it.tiles_y * ((s->L.nz + it.zc - 1) / it.zc);
@@ -612,9 +628,9 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
     tab.total_units = units;
     tab.queue = s0->queue;
     tab.done = s0->done;
-    const long long resident = 2LL * s0->num_sms;  // two CTAs per SM
+    const long long resident = (long long)shape.ctas_per_sm * s0->num_sms;
     const int grid = (int)(units < resident ? units : resident);
-    LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(s0->scheme, tab, grid, s0->st));
+    LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(shape.tx, s0->scheme, tab, grid, s0->st));
     for (int i = 0; i < n; ++i) {
       lbm_sim* s = sims[i];
       s->layers_ok[s->cur ^ 1] = 1;

@@ -16,10 +16,16 @@
 namespace lbm {
 
 constexpr int NV = 15;
-// x offset of the first interior cell inside a padded row: OX - 2 is a
-// multiple of 4, so a tile's first halo column (x0 + OX - 2, x0 a multiple of
-// 32) starts on a 16-byte boundary as a TMA copy requires.
-constexpr int OX = 6;
+// x offset of the first interior cell inside a padded row.  OX is a multiple
+// of 8 cells, so with row pitches that are multiples of 32 cells every tile
+// row (x0 a multiple of 32) starts on a 32-byte DRAM sector: the step
+// kernels' stores write whole sectors (no read-modify-write of partly
+// written sectors; measured 17% faster on 256^3 than OX = 6).  The TMA boxes
+// start TMA_LEFT = 4 cells left of the tile (x0 + OX - 4, 16-byte aligned as
+// a TMA copy requires) and are 8 cells wider than the tile.
+constexpr int OX = 8;
+constexpr int TMA_LEFT = 4;
+static_assert(OX % 8 == 0 && (OX - TMA_LEFT) % 4 == 0 && TMA_LEFT >= 2, "row alignment");
 
 // Sign pattern of the discrete velocities (Sec. 2), index order of lbm.h.
 // Magnitude: 0 for i = 0, c1 for i = 1..6, c2/sqrt(3) for i = 7..14.
@@ -206,11 +212,16 @@ cudaError_t launch_step_plain(int prec, int scheme, const void* fin, void* fout,
                               const Model<double>& md, const Model<float>& mf, unsigned* flags, cudaStream_t st);
 cudaError_t launch_step_tiled(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
                               const Model<float>& m, int zc, unsigned* flags, cudaStream_t st);
-// Pair kernel: the tiles and TMA box of the tiled kernel (kTileX x kTileY,
-// box tiled_box_x() x tiled_box_y()), two cells per thread.
-cudaError_t launch_step_pair(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                             const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
-                             unsigned wait_limit, cudaStream_t st);
+// Pair kernel (two cells per thread) on `cols` x 8 tiles: cols = 64 (box
+// 72 x 12, one CTA per SM) or 32 (the tiled kernel's tiles and box 40 x 12,
+// two CTAs per SM).  The map's box must be pair_shape(cols).bx x .by.
+struct PairShape {
+  int tx, ty, bx, by, threads, ctas_per_sm;
+};
+PairShape pair_shape(int cols);
+cudaError_t launch_step_pair(int cols, int scheme, const CUtensorMap& map, const float* fin, float* fout,
+                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc,
+                             unsigned* flags, unsigned wait_limit, cudaStream_t st);
 
 // Descriptor table of a batched step (passed by value as the kernel
 // parameter): one entry per grid, units [first_unit, first_unit +
@@ -236,8 +247,8 @@ struct BatchTable {
   unsigned long long* queue;  // next unit to take (0 at launch; reset by the last CTA)
   unsigned* done;             // CTAs finished (0 at launch; reset by the last CTA)
 };
-// Batched step over the descriptor table (same tiles and box).
-cudaError_t launch_step_pair_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st);
+// Batched step over the descriptor table (`cols` x 8 tiles, maps of that box).
+cudaError_t launch_step_pair_batch(int cols, int scheme, const BatchTable& tab, int grid, cudaStream_t st);
 // Shared-memory attributes of the tiled kernels; set once per device before
 // their first launch (not allowed inside a stream capture).
 cudaError_t prepare_tiled_kernels();

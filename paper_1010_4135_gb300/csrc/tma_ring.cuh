@@ -1,9 +1,10 @@
 // Plane-ring staging shared by the tiled step kernels (sm_103a).
 //
 // A CTA owns a TX x TY column of cells.  Each z plane of all 15 fields, with
-// a two-cell halo in x and y, arrives in shared memory through one 4D TMA
-// copy (box BX x BY x 1 x 15) into a ring of NSLOT slots, each completing on
-// its own mbarrier.  All waits are bounded (WAIT_LIMIT polls).
+// a halo of TMA_LEFT = 4 cells in x (two are read) and two in y, arrives in
+// shared memory through one 4D TMA copy (box BX x BY x 1 x 15) into a ring of
+// NSLOT slots, each completing on its own mbarrier.  All waits are bounded
+// (WAIT_LIMIT polls).
 #pragma once
 
 #include <cuda.h>
@@ -14,10 +15,10 @@ namespace lbm {
 namespace ring {
 
 constexpr int TX = 32, TY = 8;
-constexpr int BX = TX + 4, BY = TY + 4;     // tile with a 2-cell halo
-constexpr int PL = BX * BY;                 // floats per field in one plane tile
-constexpr int SLOT_BYTES_TX = NV * PL * 4;  // bytes one TMA copy delivers (25,920)
-constexpr int SLOT_STRIDE = 25984;          // slot pitch: 128-byte multiple >= SLOT_BYTES_TX
+constexpr int BX = TX + 2 * TMA_LEFT, BY = TY + 4;  // tile with its halo
+constexpr int PL = BX * BY;                          // floats per field in one plane tile
+constexpr int SLOT_BYTES_TX = NV * PL * 4;           // bytes one TMA copy delivers (28,800)
+constexpr int SLOT_STRIDE = (SLOT_BYTES_TX + 127) / 128 * 128;
 constexpr int NSLOT = 4;
 constexpr int SMEM_BYTES = NSLOT * SLOT_STRIDE + NSLOT * 8;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // try_wait polls before giving up (seconds)
@@ -61,6 +62,15 @@ __device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* ma
       " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Ask the TMA unit to bring a plane tile into L2 ahead of its shared-memory
+// copy (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_plane(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(0)
+               : "memory");
 }
 
 }  // namespace ring

@@ -105,10 +105,12 @@ class Sim:
 
     def set_launch(self, variant="tiled", zchunk: int = 0):
         """FP32 step kernel: "tiled" (32 x 8 TMA plane tiles, cell pairs, boundary layers
-        written by the step; default), "tiled_fill" (boundary layers by a fill launch),
-        "tiled_single" (one cell per thread) or "plain"; zchunk = z planes per CTA (0 = auto)."""
+        written by the step; default), "tiled64" (the same on 64 x 8 tiles), "tiled_fill"
+        (boundary layers by a fill launch), "tiled_single" (one cell per thread) or "plain";
+        zchunk = z planes per CTA (0 = auto)."""
         v = {"tiled": A.LBM_VARIANT_TILED, "plain": A.LBM_VARIANT_PLAIN,
-             "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL}[variant] \
+             "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL,
+             "tiled64": A.LBM_VARIANT_TILED64}[variant] \
             if isinstance(variant, str) else int(variant)
         A.check(A.lbm_set_launch(self._h, v, int(zchunk)), "lbm_set_launch")
         self.launch = (variant, int(zchunk))

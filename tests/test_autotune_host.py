@@ -21,20 +21,22 @@ def test_key_names_device_grid_precision_scheme_and_boundaries():
 
 def test_cached_choice_is_applied_without_measuring(tmp_path, monkeypatch):
     path = str(tmp_path / "launch.json")
-    autotune._store(path, "K", {"zchunk": 24, "ms": 0.5, "timings": {"24": 0.5}})
+    autotune._store(path, "K", {"variant": "tiled64", "zchunk": 24, "ms": 0.5, "timings": {"tiled64:24": 0.5}})
     monkeypatch.setattr(autotune, "measure", lambda *a, **k: (_ for _ in ()).throw(AssertionError("measured")))
     s = FakeSim()
     r = autotune._tune([s], autotune.ZCHUNKS, 10, True, path, batched=False, key="K")
-    assert r["cached"] and r["zchunk"] == 24 and s.launch == ("tiled", 24)
+    assert r["cached"] and r["zchunk"] == 24 and s.launch == ("tiled64", 24)
 
 
 def test_fastest_candidate_is_chosen_and_stored(tmp_path, monkeypatch):
     path = str(tmp_path / "launch.json")
-    monkeypatch.setattr(autotune, "measure", lambda sims, zcs, steps, batched: {4: 0.9, 16: 0.5, 32: 0.6})
+    monkeypatch.setattr(autotune, "measure", lambda sims, zcs, steps, batched, variants:
+                        {("tiled", 4): 0.9, ("tiled", 16): 0.55, ("tiled64", 16): 0.5, ("tiled64", 32): 0.6})
     s = FakeSim()
     r = autotune._tune([s], (4, 16, 32), 10, True, path, batched=False, key="K2")
-    assert not r["cached"] and r["zchunk"] == 16 and s.launch == ("tiled", 16)
-    assert json.load(open(path))["K2"]["zchunk"] == 16
+    assert not r["cached"] and (r["variant"], r["zchunk"]) == ("tiled64", 16) and s.launch == ("tiled64", 16)
+    rec = json.load(open(path))["K2"]
+    assert rec["zchunk"] == 16 and rec["variant"] == "tiled64" and rec["timings"]["tiled:4"] == 0.9
 
 
 def test_fp64_sims_are_not_tuned(tmp_path):
