@@ -188,6 +188,60 @@ def high_mach_tube(nx=2000, ny=4, nz=4):
                       12.0, 36.0, 20.0, 2e-6, 2e-6, 15980)
 
 
+# The paper's own runs (Sec. 4) at the sizes it prints.
+PAPER_HM_LEFT = (100.0, 10.0, 0.0, 0.0, 0.714286)
+PAPER_HM_RIGHT = (150.0, 0.0, 0.0, 0.0, 50.0)
+
+
+def paper_high_mach_tube():
+    """The paper's high-Mach tube (Fig. 7): left (100, 10, 0, 0, 0.714286), a
+    Mach-10 flow, right (150, 0, 0, 0, 50); (c1, c2, eta0) = (8, 24, 8), dx =
+    0.01, dt = tau = 1e-5, t = 0.25 (25,000 steps).  The domain length is not
+    printed: 300 cells on [0, 3] with the interface at x = 0.5 hold the waves
+    (left shock -0.55, right shock +9.17 per unit time) until t = 0.25."""
+    return shock_tube("paper_high_mach_tube_300x4x4", 300, 4, 4, 0.01, PAPER_HM_LEFT, PAPER_HM_RIGHT, 0.5,
+                      8.0, 24.0, 8.0, 1e-5, 1e-5, 25000)
+
+
+PAPER_BUBBLE_RHO = {"light": 0.1358, "heavy": 4.1538}
+
+
+def paper_shock_bubble(kind="light", radius_cells=25, shock_cell=250):
+    """The paper's 3D run (Sec. 4(2), Figs. 8-10): 300 x 80 x 80 cells of dx =
+    0.001, (c1, c2, eta0) = (2, 6, 4), dt = tau = 1e-5, t = 0.1 (10,000
+    steps).  Pre-shock gas (1, 0, 0, 0, 1); a Mach-2 shock moving in -x with
+    the post-shock state (2.66667, -1.47902, 0, 0, T = 4.5 / 2.66667) behind
+    it (x > shock); a bubble of rho 0.1358 (light) or 4.1538 (heavy) at p = 1
+    centred at cell (200, 40, 40).  Boundaries as printed: x-hi holds the
+    post-shock state, x-lo extrapolates, the four y / z faces reflect.  The
+    bubble radius and the initial shock position are not printed: radius 25
+    cells, shock at cell 250.  The bubble surface is one cell thick."""
+    nx, ny, nz, dx = 300, 80, 80, 0.001
+    r2, u2, p2, D = rankine_hugoniot(2.0)
+    post = state_from_p(r2, -u2, 0.0, 0.0, p2)
+    amb = state_from_p(1.0, 0.0, 0.0, 0.0, 1.0)
+    sph = state_from_p(PAPER_BUBBLE_RHO[kind], 0.0, 0.0, 0.0, 1.0)
+    w = Workload(name=f"paper_shock_bubble_{kind}_300x80x80", nx=nx, ny=ny, nz=nz, dx=dx, c1=2.0, c2=6.0, eta0=4.0,
+                 dt=1e-5, tau=1e-5, steps=10000, gamma=GAMMA,
+                 bc_lo=(EXTRAPOLATE, REFLECT, REFLECT), bc_hi=(FIXED, REFLECT, REFLECT),
+                 fixed_hi=(post, (0.0,) * 5, (0.0,) * 5),
+                 meta={"ambient": amb, "sphere": sph, "post": post, "centre": ((200 + 0.5) * dx, 40 * dx, 40 * dx),
+                       "radius": radius_cells * dx, "mach": 2.0, "shock_speed": D, "width": 1.0,
+                       "shock_x": shock_cell * dx})
+    w.ic = _paper_bubble_ic
+    return w
+
+
+def _paper_bubble_ic(w: Workload):
+    rho, u, T = _sphere_ic(w)
+    post = w.meta["post"]
+    behind = (cell_centres(w.nx, w.dx) >= w.meta["shock_x"])[None, None, :] & np.ones(rho.shape, dtype=bool)
+    rho = np.where(behind, post[0], rho)
+    u = np.stack([np.where(behind, post[1 + a], u[a]) for a in range(3)])
+    T = np.where(behind, post[4], T)
+    return rho, u, T
+
+
 def shock_droplet(n=256):
     """Mach-2 shock into a rho = 5 droplet (radius 0.1, centre (0.3, 0.5, 0.5))
     on the unit cube, n^3 cells; (c1, c2, eta0) = (2, 6, 4), dt = tau = 5e-5,
