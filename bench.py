@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--requests", type=int, default=200, help="serve: number of requests in the trace")
     p.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     p.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serve: workspace budget (0 = 80%% of free)")
+    p.add_argument("--l1-sample", type=float, default=0.0,
+                   help="serve: fraction of requests (seeded) checked against the FP64 path (0 = the three smallest)")
     p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "serve"],
                    help="droplet: 256^3 Mach-2 shock-droplet; bubble: 512x256x256 Mach-3 shock-bubble; "
                         "batch: the bubble grid plus 8 128^3 copies with seeded Mach numbers, one launch per "
@@ -468,10 +470,17 @@ def run_serve(args):
     trace = workloads.serving_trace(seed=5, n=args.requests, rate=args.rate)
     budget = int(args.hbm_budget_gb * 2 ** 30) if args.hbm_budget_gb > 0 else None
     srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True)
+    srv.tune_shapes(workloads.SERVING_GRIDS)  # before the trace starts: the server's grid menu
     done = srv.run(trace)
     stats = serve.summary(done, srv.wall)
-    # L1(rho) of the three smallest finished requests against the FP64 path
-    sample = sorted(done, key=lambda j: (int(np.prod(j.req["grid"])) * j.req["steps"], j.req["id"]))[:3]
+    # L1 / Linf of rho against the FP64 path (itself parity-checked against the oracle):
+    # a seeded sample of the finished requests, or the three smallest
+    if args.l1_sample > 0:
+        k = max(1, int(round(args.l1_sample * len(done))))
+        pick = np.random.default_rng(11).choice(len(done), size=k, replace=False)
+        sample = [done[i] for i in sorted(pick)]
+    else:
+        sample = sorted(done, key=lambda j: (int(np.prod(j.req["grid"])) * j.req["steps"], j.req["id"]))[:3]
     l1 = []
     for j in sample:
         w = workloads.request_workload(j.req, *j.params)
@@ -481,8 +490,10 @@ def run_serve(args):
         s.step(j.req["steps"])
         r64, _, _ = s.moments()
         s.close()
-        l1.append({"id": j.req["id"], "grid": list(j.req["grid"]), "steps": j.req["steps"], "mach": j.req["mach"],
-                   "l1_rho": float(np.abs(j.rho - r64).sum() / np.abs(r64).sum())})
+        l1.append({"id": j.req["id"], "kind": j.req["kind"], "grid": list(j.req["grid"]), "steps": j.req["steps"],
+                   "mach": j.req["mach"], "ratio": j.req["ratio"], "health": j.health,
+                   "l1_rho": float(np.abs(j.rho - r64).sum() / np.abs(r64).sum()),
+                   "linf_rho": float(np.abs(j.rho - r64).max() / np.abs(r64).max())})
     line = {
         "metric": METRIC, "value": stats["cell_updates_per_s"], "unit": UNIT, "n_gpus": 1,
         "steps": int(sum(j.req["steps"] for j in done)), "warmup": 0,
@@ -491,8 +502,13 @@ def run_serve(args):
         "config": {"workload": f"serving: {args.requests} requests, Poisson rate {args.rate}/s (seed 5), grids "
                                "64^3..256^3, Mach U[1.2,10], density ratio log-U[0.1,10], 500-3000 steps, FP32",
                    "hbm_budget_bytes": srv.budget, "peak_resident_bytes": srv.peak_bytes,
-                   "peak_batch": srv.peak_batch},
+                   "peak_batch": srv.peak_batch, "host_seconds": dict(srv.host_s),
+                   "l1_sample": (f"seeded {args.l1_sample:.0%} of the finished requests" if args.l1_sample > 0
+                                 else "the three smallest finished requests")},
         "serving": stats, "l1_vs_fp64_sample": l1, "gpu_launches": srv.launches,
+        "unhealthy_requests": [{"id": j.req["id"], "kind": j.req["kind"], "grid": list(j.req["grid"]),
+                                "mach": j.req["mach"], "ratio": j.req["ratio"], "c1_c2_eta0_dt": list(j.params),
+                                "health": j.health} for j in done if j.health],
     }
     print(json.dumps(line), flush=True)
     return 0

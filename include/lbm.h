@@ -200,6 +200,16 @@ LBM_API int lbm_conserved_noalloc(const void* f, int32_t precision, int32_t nx, 
  * (LBM_HEALTH_TIMEOUT), else LBM_ENONFINITE when any other bit is set. */
 LBM_API int lbm_health(lbm_sim* sim, uint32_t* flags);
 
+/* Stream-ordered forms for callers that keep the GPU busy (a serving loop):
+ * nothing synchronises; completion is observed with an event recorded on
+ * the sim's stream after the call.  lbm_moments_async writes rho, u, T
+ * ([nz][ny][nx], u as 3 such planes, FP64) to device memory; lbm_health_async
+ * copies the health bits to `flags` (device memory or page-locked host
+ * memory; valid once the stream reaches this point).  The paper has no
+ * counterpart.  Errors: LBM_EINVAL (NULL pointers), LBM_ECUDA. */
+LBM_API int lbm_moments_async(lbm_sim* sim, double* rho, double* u, double* T);
+LBM_API int lbm_health_async(lbm_sim* sim, uint32_t* flags);
+
 /* Wait for the sim's stream; reports asynchronous kernel faults. */
 LBM_API int lbm_sync(lbm_sim* sim);
 

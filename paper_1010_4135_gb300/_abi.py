@@ -56,6 +56,8 @@ SIGNATURES = [
     ("lbm_graph_launch", ctypes.c_int, [_vp]),
     ("lbm_graph_destroy", None, [_vp]),
     ("lbm_moments", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),
+    ("lbm_moments_async", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("lbm_health_async", ctypes.c_int, [_vp, _vp]),
     ("lbm_get_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     ("lbm_set_f", ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     ("lbm_conserved", ctypes.c_int, [_vp, _dp]),
@@ -123,6 +125,8 @@ lbm_graph_capture = _forward("lbm_graph_capture")
 lbm_graph_launch = _forward("lbm_graph_launch")
 lbm_graph_destroy = _forward("lbm_graph_destroy")
 lbm_moments = _forward("lbm_moments")
+lbm_moments_async = _forward("lbm_moments_async")
+lbm_health_async = _forward("lbm_health_async")
 lbm_get_f = _forward("lbm_get_f")
 lbm_set_f = _forward("lbm_set_f")
 lbm_conserved = _forward("lbm_conserved")

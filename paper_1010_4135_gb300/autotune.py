@@ -50,12 +50,15 @@ def _store(path, key, value):
         os.replace(tmp, path)
 
 
-def key_of(sims, batched: bool, device_name: str | None = None, sms: int | None = None) -> str:
-    """Cache key: device, SM count, and per sim the grid, precision, scheme and boundary kinds."""
+def key_of(sims, batched: bool, device_name: str | None = None, sms: int | None = None,
+           variants=None) -> str:
+    """Cache key: device, SM count, the candidate tile shapes, and per sim the
+    grid, precision, scheme and boundary kinds."""
     if device_name is None or sms is None:
         props = torch.cuda.get_device_properties(sims[0].device)
         device_name, sms = props.name, props.multi_processor_count
-    parts = [device_name.replace(" ", "_"), str(int(sms)), "batch" if batched else "single"]
+    parts = [device_name.replace(" ", "_"), str(int(sms)), "batch" if batched else "single",
+             ",".join(variants or VARIANTS)]
     for s in sims:
         c = s.config
         parts.append("x".join(str(int(v)) for v in (c["nx"], c["ny"], c["nz"])) + f":{c['precision']}:{c['scheme']}:"
@@ -121,7 +124,7 @@ def _tune(sims, zchunks, steps, use_cache, path, batched, key=None, variants=VAR
     if any(s.config["precision"] not in ("fp32", 1) for s in sims):
         return {"variant": None, "zchunk": None, "ms": None, "cached": False, "timings": {}}
     path = path or cache_path()
-    key = key or key_of(sims, batched)
+    key = key or key_of(sims, batched, variants=variants)
     hit = _load(path).get(key) if use_cache else None
     if hit is not None:
         for s in sims:

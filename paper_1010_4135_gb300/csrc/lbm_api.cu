@@ -865,6 +865,22 @@ int lbm_health(lbm_sim* s, uint32_t* flags_out) {
   return flags ? LBM_ENONFINITE : LBM_OK;
 }
 
+int lbm_moments_async(lbm_sim* s, double* rho, double* u, double* T) {
+  int rc = enter(s);
+  if (rc) return rc;
+  if (!rho || !u || !T) return LBM_EINVAL;
+  LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_moments(s->prec, s->fbuf[s->cur], s->L, s->md, rho, u, T, s->st));
+  return LBM_OK;
+}
+
+int lbm_health_async(lbm_sim* s, uint32_t* flags_out) {
+  int rc = enter(s);
+  if (rc) return rc;
+  if (!flags_out) return LBM_EINVAL;
+  LBM_CK(s, cudaMemcpyAsync(flags_out, s->flags, sizeof(unsigned), cudaMemcpyDefault, s->st));
+  return LBM_OK;
+}
+
 int lbm_sync(lbm_sim* s) {
   int rc = enter(s);
   if (rc) return rc;

@@ -1,17 +1,25 @@
 """Continuous-batching solve server.
 
 Requests (shock tubes and shock-sphere solves of different grids, Mach
-numbers and density ratios) arrive over time.  The server admits a request
-when it has arrived, a batch slot is free and its workspace fits the HBM
-budget; admitted grids stay resident and advance together, one batched tile
-kernel launch per time step covering every resident grid (lbm_step_batch).
-A request retires after its own number of steps: its moments are copied to
-the host, its workspace is released, and waiting requests are admitted in
-arrival order.  Latency is measured from arrival to retirement.
+numbers and density ratios) arrive over time.  On arrival a worker thread
+prepares each request off the serving loop: its parameters (the von Neumann
+rule of stability.py) and its initial fields.  The loop admits a prepared
+request when a batch slot is free and its workspace fits the HBM budget;
+admitted grids stay resident and advance together, one batched tile kernel
+launch per time step covering every resident grid (lbm_step_batch).
+
+The loop never drains the GPU to make progress: steps are launched a tick
+(at most `tick` steps) at a time with at most two ticks in flight; a
+request that has run its steps gets its moments and health bits queued on
+the stream (lbm_moments_async / lbm_health_async into page-locked memory)
+and an event recorded behind them; its workspace is released once that
+event has completed, and its latency ends there (arrival to results on the
+host).  Waiting requests are admitted in arrival order.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import ctypes
 import dataclasses
 import time
@@ -29,14 +37,21 @@ from . import stability
 @dataclasses.dataclass
 class Job:
     req: dict
-    params: tuple
-    sim: object = None
     nbytes: int = 0
+    prep: object = None        # future of (params, workload, (rho, u, T) page-locked)
+    fields: tuple = None       # the page-locked initial fields while their copy is in flight
+    params: tuple = None
+    sim: object = None
     remaining: int = 0
     admitted: float = 0.0
     finished: float = 0.0
     health: int = 0
     rho: object = None
+    # retirement in flight
+    event: object = None
+    out: tuple = None          # device (rho, u, T) of the final state
+    host_rho: object = None    # page-locked copy of rho
+    host_flags: object = None  # page-locked health bits
 
 
 def request_parameters(req):
@@ -52,6 +67,15 @@ def request_parameters(req):
     return c1, c2, eta0, dt
 
 
+def prepare(req):
+    """Host work of one request: parameters, workload and initial fields (in
+    page-locked memory, ready for an asynchronous copy)."""
+    params = request_parameters(req)
+    w = workloads.request_workload(req, *params)
+    fields = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.initial_fields())
+    return params, w, fields
+
+
 def workspace_bytes(grid, precision=A.LBM_FP32) -> int:
     g = A.make_grid(*grid)
     return int(A.lbm_workspace_bytes(ctypes.byref(g), precision))
@@ -60,10 +84,16 @@ def workspace_bytes(grid, precision=A.LBM_FP32) -> int:
 class Server:
     """hbm_budget: bytes of workspace the resident grids may hold together
     (default: 80% of the device's free memory); tick: most steps launched
-    between two retirement checks; tune: give each admitted grid the z chunk
-    the autotuner measured for its shape (once per shape, then cached)."""
+    per batched launch sequence between two looks at the queue; tune: give
+    each admitted grid the launch configuration the autotuner measured for
+    its shape (once per shape, then cached; `tune_shapes` does it ahead).
+    One batched launch runs one kernel, so every grid keeps the default tile
+    shape and only its z chunk is tuned."""
 
-    def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False, tune=True):
+    VARIANT = ("tiled",)
+
+    def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False, tune=True,
+                 prep_workers=2):
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(0.8 * free)
@@ -72,80 +102,158 @@ class Server:
         self.tick = int(tick)
         self.keep_results = keep_results
         self.tune = tune
+        self.prep_workers = int(prep_workers)
+        self.stream = torch.cuda.Stream()
         self.peak_bytes = 0
         self.peak_batch = 0
         self.launches = 0
+        self.host_s = collections.Counter()  # host seconds by activity
+
+    def tune_shapes(self, grids):
+        """Autotune each grid shape once before serving (cached per shape)."""
+        if not self.tune:
+            return
+        for g in grids:
+            w = workloads.request_workload({"id": -1, "grid": tuple(g), "mach": 2.0, "ratio": 1.0,
+                                            "steps": 1, "kind": "sphere"}, 2.0, 6.0, 4.0, 1e-5)
+            s = S.from_workload(w, precision="fp32", stream=self.stream)
+            s.init(*w.initial_fields())
+            autotune.tune(s, variants=self.VARIANT)
+            s.close()
 
     def _admit(self, job: Job):
-        w = workloads.request_workload(job.req, *job.params)
-        s = S.from_workload(w, precision="fp32")
-        rho, u, T = w.initial_fields()
-        s.init(rho, u, T)
+        params, w, fields = job.prep.result()
+        job.params = params
+        job.fields = fields
+        s = S.from_workload(w, precision="fp32", stream=self.stream)
+        with torch.cuda.stream(self.stream):
+            rho, u, T = (f.to(s.device, non_blocking=True) for f in fields)
+        s.init(rho, u, T)  # device pointers: stream-ordered, no synchronisation
         if self.tune:
-            autotune.tune(s)
+            autotune.tune(s, variants=self.VARIANT)
         job.sim = s
         job.remaining = job.req["steps"]
+
+    def _retire_start(self, job: Job):
+        """Queue the final moments and health bits behind the job's steps."""
+        s = job.sim
+        nz, ny, nx = s.shape
+        with torch.cuda.stream(self.stream):
+            rho = torch.empty((nz, ny, nx), dtype=torch.float64, device=s.device)
+            u = torch.empty((3, nz, ny, nx), dtype=torch.float64, device=s.device)
+            T = torch.empty((nz, ny, nx), dtype=torch.float64, device=s.device)
+            flags = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+            A.check(A.lbm_moments_async(s.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                        ctypes.c_void_p(T.data_ptr())), "lbm_moments_async")
+            A.check(A.lbm_health_async(s.handle, ctypes.c_void_p(flags.data_ptr())), "lbm_health_async")
+            host_rho = torch.empty(rho.shape, dtype=torch.float64, pin_memory=True)
+            host_rho.copy_(rho, non_blocking=True)
+            job.event = torch.cuda.Event()
+            job.event.record(self.stream)
+        job.out = (rho, u, T)
+        job.host_flags = flags
+        job.host_rho = host_rho
 
     def run(self, trace, time_scale: float = 1.0):
         """Serve `trace` (arrival times scaled by time_scale) in real time; returns the finished jobs."""
         pending = collections.deque(sorted(trace, key=lambda r: r["arrival"]))
-        jobs_waiting: collections.deque = collections.deque()
+        waiting: collections.deque = collections.deque()
         active: list = []
+        retiring: list = []
         done: list = []
+        ticks: collections.deque = collections.deque()  # events of launched ticks
         used = 0
+        pool = cf.ThreadPoolExecutor(max_workers=self.prep_workers)
         t0 = time.perf_counter()
-        while pending or jobs_waiting or active:
-            now = time.perf_counter() - t0
-            while pending and pending[0]["arrival"] * time_scale <= now:
-                r = pending.popleft()
-                jobs_waiting.append(Job(req=r, params=request_parameters(r), nbytes=workspace_bytes(r["grid"])))
-            # admission in arrival order, by footprint and batch slots
-            while jobs_waiting and len(active) < self.max_batch and used + jobs_waiting[0].nbytes <= self.budget:
-                j = jobs_waiting.popleft()
-                self._admit(j)
-                j.admitted = time.perf_counter() - t0
-                used += j.nbytes
-                active.append(j)
-            if jobs_waiting and not active and jobs_waiting[0].nbytes > self.budget:
-                raise RuntimeError(f"request {jobs_waiting[0].req['id']} exceeds the HBM budget")
-            self.peak_bytes = max(self.peak_bytes, used)
-            self.peak_batch = max(self.peak_batch, len(active))
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, pending[0]["arrival"] * time_scale - (time.perf_counter() - t0)))
-                continue
-            n = min(self.tick, min(j.remaining for j in active))
-            S.step_batch([j.sim for j in active], n)
-            self.launches += n
-            for j in active:
-                j.remaining -= n
-            still = []
-            for j in active:
-                if j.remaining > 0:
-                    still.append(j)
+
+        def clock():
+            return time.perf_counter() - t0
+
+        try:
+            while pending or waiting or active or retiring:
+                h = time.perf_counter()
+                while pending and pending[0]["arrival"] * time_scale <= clock():
+                    r = pending.popleft()
+                    waiting.append(Job(req=r, nbytes=workspace_bytes(r["grid"]), prep=pool.submit(prepare, r)))
+                # admission in arrival order, by footprint and batch slots, once prepared
+                while (waiting and waiting[0].prep.done() and len(active) < self.max_batch
+                       and used + waiting[0].nbytes <= self.budget):
+                    j = waiting.popleft()
+                    self._admit(j)
+                    j.admitted = clock()
+                    used += j.nbytes
+                    active.append(j)
+                if waiting and not active and not retiring and waiting[0].nbytes > self.budget:
+                    raise RuntimeError(f"request {waiting[0].req['id']} exceeds the HBM budget")
+                self.host_s["admit"] += time.perf_counter() - h
+                self.peak_bytes = max(self.peak_bytes, used)
+                self.peak_batch = max(self.peak_batch, len(active))
+                # results that have reached the host free their workspace
+                h = time.perf_counter()
+                still = []
+                for j in retiring:
+                    if j.event.query():
+                        j.finished = clock()
+                        j.health = int(j.host_flags[0])
+                        if self.keep_results:
+                            j.rho = j.host_rho.numpy()
+                        j.sim.close()
+                        j.sim, j.out, j.host_rho, j.fields = None, None, None, None
+                        used -= j.nbytes
+                        done.append(j)
+                    else:
+                        still.append(j)
+                retiring = still
+                self.host_s["retire"] += time.perf_counter() - h
+                if active:
+                    # at most two ticks in flight: wait for the older one
+                    h = time.perf_counter()
+                    while len(ticks) >= 2:
+                        ticks.popleft().synchronize()
+                    self.host_s["wait_gpu"] += time.perf_counter() - h
+                    h = time.perf_counter()
+                    n = min(self.tick, min(j.remaining for j in active))
+                    S.step_batch([j.sim for j in active], n)
+                    self.launches += n
+                    still = []
+                    for j in active:
+                        j.remaining -= n
+                        if j.remaining > 0:
+                            still.append(j)
+                        else:
+                            self._retire_start(j)
+                            retiring.append(j)
+                    active = still
+                    ev = torch.cuda.Event()
+                    ev.record(self.stream)
+                    ticks.append(ev)
+                    self.host_s["launch"] += time.perf_counter() - h
                     continue
-                j.health = j.sim.health()
-                rho, _, _ = j.sim.moments()  # synchronises
-                j.finished = time.perf_counter() - t0
-                if self.keep_results:
-                    j.rho = rho
-                j.sim.close()
-                j.sim = None
-                used -= j.nbytes
-                done.append(j)
-            active = still
-        self.wall = time.perf_counter() - t0
+                # nothing to step: wait for a retirement, a preparation or the next arrival
+                h = time.perf_counter()
+                if retiring:
+                    retiring[0].event.synchronize()
+                elif waiting:
+                    cf.wait([waiting[0].prep], timeout=0.05)
+                elif pending:
+                    time.sleep(max(0.0, min(0.05, pending[0]["arrival"] * time_scale - clock())))
+                self.host_s["idle"] += time.perf_counter() - h
+        finally:
+            pool.shutdown(wait=True)
+        self.wall = clock()
         return done
 
 
 def summary(done, wall, time_scale=1.0):
     lat = np.array([j.finished - j.req["arrival"] * time_scale for j in done])
+    queue = np.array([j.admitted - j.req["arrival"] * time_scale for j in done])
     cells = sum(int(np.prod(j.req["grid"])) * j.req["steps"] for j in done)
     return {
         "requests": len(done),
         "p50_latency_s": float(np.percentile(lat, 50)),
         "p99_latency_s": float(np.percentile(lat, 99)),
         "mean_latency_s": float(lat.mean()),
+        "p50_queue_s": float(np.percentile(queue, 50)),
         "solves_per_s": len(done) / wall,
         "cell_updates_per_s": cells / wall,
         "wall_s": wall,

@@ -15,7 +15,8 @@ class FakeSim:
 
 def test_key_names_device_grid_precision_scheme_and_boundaries():
     k = autotune.key_of([FakeSim(), FakeSim()], True, device_name="NVIDIA GB300", sms=152)
-    assert k == "NVIDIA_GB300|152|batch|64x32x16:fp32:nnd:100200|64x32x16:fp32:nnd:100200"
+    assert k == "NVIDIA_GB300|152|batch|tiled,tiled64|64x32x16:fp32:nnd:100200|64x32x16:fp32:nnd:100200"
+    assert autotune.key_of([FakeSim()], False, "d", 1, variants=("tiled",)) != autotune.key_of([FakeSim()], False, "d", 1)
     assert autotune.key_of([FakeSim()], False, "d", 1) != autotune.key_of([FakeSim()], True, "d", 1)
 
 
