@@ -169,21 +169,32 @@ def courant(c2: float, dt: float, dx: float) -> float:
     return c2 / math.sqrt(3.0) * dt / dx
 
 
-def choose_parameters(states, dx, gamma=1.4, tol=1e-3, candidates=DT_CANDIDATES, courant_max=COURANT_MAX):
+def choose_parameters(states, dx, gamma=1.4, tol=1e-3, candidates=DT_CANDIDATES, courant_max=COURANT_MAX,
+                      c1_factors=(1.0, 1.1, 1.2, 1.35, 1.5)):
     """(c1, c2, eta0, dt) for a run whose fastest material speed is set by the
-    given states: c1 = max(2, ceil(1.2 max|u|)), c2 = 3 c1, eta0 = 2 c1 (the
-    paper's advice: c1 near the largest flow speed, c2 about 3 c1, eta0 1-2 c1),
-    and dt = tau the largest candidate with max|omega| <= 1 + tol and a
-    diagonal Courant number <= courant_max.  The von Neumann criterion is a
-    linear one; strong shocks also need the small Courant numbers the paper's
-    runs use (0.01-0.035): 1D runs of Mach 2-10 shocks stay positive up to
-    0.05 with this c1 rule and fail for some at 0.15."""
+    given states, following the paper's advice (c1 near the largest flow
+    speed, c2 about 3 c1, eta0 1-2 c1): c2 = 3 c1, eta0 = 2 c1, and c1 the
+    smallest of max(2, ceil(f max|u|)) over the factors f for which some dt =
+    tau among the candidates has max|omega| <= 1 + tol and a diagonal Courant
+    number <= courant_max (the largest such dt).  The smallest stable c1
+    matters beyond the linear criterion: at a density jump into cold gas the
+    populations of large c1 carry negative energy across (T < 0 near the
+    interface within tens of steps once c1^2 / T is near 100), and strong
+    shocks need the small Courant numbers of the paper's runs (0.01-0.035):
+    1D runs of Mach 2-10 shocks stay positive up to 0.05 and fail for some at
+    0.15.  Returns dt = None when no candidate passes."""
     umax = max(math.sqrt(sum(float(x) ** 2 for x in st[1:4])) for st in states)
-    c1 = float(max(2, math.ceil(1.2 * umax)))
-    c2, eta0 = 3.0 * c1, 2.0 * c1
-    for dt in sorted(candidates, reverse=True):
-        if courant(c2, dt, dx) > courant_max:
+    tried = []
+    for f in c1_factors:
+        c1 = float(max(2, math.ceil(f * umax)))
+        if c1 in tried:
             continue
-        if max_growth(states, c1, c2, eta0, gamma, dt, dt, dx, nk=24) <= 1.0 + tol:
-            return c1, c2, eta0, dt
-    return c1, c2, eta0, None
+        tried.append(c1)
+        c2, eta0 = 3.0 * c1, 2.0 * c1
+        for dt in sorted(candidates, reverse=True):
+            if courant(c2, dt, dx) > courant_max:
+                continue
+            if max_growth(states, c1, c2, eta0, gamma, dt, dt, dx, nk=24) <= 1.0 + tol:
+                return c1, c2, eta0, dt
+    c1 = tried[-1]
+    return c1, 3.0 * c1, 2.0 * c1, None

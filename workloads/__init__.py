@@ -329,19 +329,21 @@ def request_states(req):
     return pre, post, other
 
 
-def request_workload(req, c1, c2, eta0, dt):
+def request_workload(req, c1, c2, eta0, dt, width=3.0):
     """The Workload of a request with the given model constants.  Tube: the
     post-shock state (x < 0.3 of the domain) against gas of the request's
     density ratio; sphere: the shock entering at x = 0 into ambient gas holding
     a sphere of that density (radius 0.1 L_y, centre (0.3 L_x, 0.5, 0.5)).
-    Both interfaces are one cell thick (interface_weight)."""
+    Both interfaces are `width` cells thick (interface_weight): served
+    requests reach Mach 10 into gas ten times lighter or heavier, where a
+    one-cell jump can drive T below zero at the interface."""
     nx, ny, nz = req["grid"]
     dx = 1.0 / ny
     pre, post, other = request_states(req)
     if req["kind"] == "tube":
         w = shock_tube(f"req{req['id']}_tube", nx, ny, nz, dx, post, other, 0.3 * nx * dx, c1, c2, eta0, dt, dt,
-                       req["steps"], width=1.0)
+                       req["steps"], width=width)
     else:
         w = shock_sphere(f"req{req['id']}_sphere", nx, ny, nz, dx, req["mach"], req["ratio"], 0.1,
-                         (0.3 * nx * dx, 0.5, 0.5), c1, c2, eta0, dt, dt, req["steps"])
+                         (0.3 * nx * dx, 0.5, 0.5), c1, c2, eta0, dt, dt, req["steps"], width=width)
     return w
