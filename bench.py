@@ -279,9 +279,10 @@ def gpu_smi_id(torch, dev):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_rate(w, steps, nz_slab=None):
+def cpu_oracle_rate(w, steps, nz_slab=None, nthreads=None):
     """cell-updates/s of the FP64 oracle on the same workload (optionally a z-slab
-    of nz_slab planes with the workload's x/y extent and boundaries)."""
+    of nz_slab planes with the workload's x/y extent and boundaries), on
+    nthreads threads (default: all host cores)."""
     import numpy as np
     import oracle
     ww = w if nz_slab is None else w.with_grid(w.nx, w.ny, nz_slab, dx=w.dx)
@@ -289,7 +290,7 @@ def cpu_oracle_rate(w, steps, nz_slab=None):
     rho, u, T = ww.initial_fields()
     f = oracle.init(cfg, rho, u, T)
     del rho, u, T
-    nthreads = os.cpu_count() or 1
+    nthreads = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
     f = oracle.run(cfg, f, steps, nthreads)
     dt = time.perf_counter() - t0
@@ -431,9 +432,12 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu and world == 1:
         rate, cores, ww, dt = cpu_oracle_rate(w, args.cpu_steps)
+        rate1, _, ww1, dt1 = cpu_oracle_rate(w, 2, nz_slab=4, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_steps} FP64 oracle steps of the full {w.nx}x{w.ny}x{w.nz} grid "
-                         f"({dt:.1f} s)"}
+                         f"({dt:.1f} s)",
+               "value_1thread": rate1,
+               "sample_1thread": f"2 steps of a {ww1.nx}x{ww1.ny}x4 slab on 1 thread ({dt1:.1f} s)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
