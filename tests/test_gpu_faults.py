@@ -82,3 +82,31 @@ def test_checkpoint_resume_is_bitwise(precision, variant):
     c.set_f(ck)
     c.step(8)
     assert np.array_equal(a.get_f(), c.get_f())
+
+
+def test_stream_ordered_moments_and_health_match_the_synchronising_calls():
+    """lbm_moments_async / lbm_health_async queue their work behind the steps
+    without synchronising; after an event they equal lbm_moments / lbm_health."""
+    import torch
+    from paper_1010_4135_gb300 import _abi as A
+    cfg = case_cfg("fixed_extrap_reflect_33x17x9")
+    s = sim_for(cfg, "fp32")
+    s.set_f(initial_f(cfg, seed=73).astype(np.float32))
+    s.step(5)
+    nz, ny, nx = s.shape
+    rho = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    T = torch.empty((nz, ny, nx), dtype=torch.float64, device="cuda")
+    flags = torch.full((1,), 77, dtype=torch.int32, pin_memory=True)
+    A.check(A.lbm_moments_async(s.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                ctypes.c_void_p(T.data_ptr())), "lbm_moments_async")
+    A.check(A.lbm_health_async(s.handle, ctypes.c_void_p(flags.data_ptr())), "lbm_health_async")
+    ev = torch.cuda.Event()
+    ev.record(s.stream)
+    ev.synchronize()
+    r2, u2, T2 = s.moments()
+    assert np.array_equal(rho.cpu().numpy(), r2) and np.array_equal(u.cpu().numpy(), u2)
+    assert np.array_equal(T.cpu().numpy(), T2)
+    assert int(flags[0]) == s.health() == 0
+    assert A.lbm_moments_async(s.handle, None, None, None) == A.LBM_EINVAL
+    assert A.lbm_health_async(s.handle, None) == A.LBM_EINVAL
