@@ -259,10 +259,22 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   if (!last) return;
   __threadfence();
   {
-    const int i = threadIdx.x & 15, j = threadIdx.x >> 4;  // field i, strided part j of 16
+    // field i, strided part j of 16; the partials are read through L2 (the
+    // other blocks' writes are ordered before their counter increments),
+    // eight loads in flight per step of the fixed-order sum
+    const int i = threadIdx.x & 15, j = threadIdx.x >> 4;
     double t = 0.0;
-    if (i < NV)
-      for (unsigned b = j; b < gridDim.x; b += 16) t += ((volatile double*)partials)[b * 16 + i];
+    if (i < NV) {
+      unsigned b = j;
+      for (; b + 7 * 16 < gridDim.x; b += 8 * 16) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldcg(partials + (b + q * 16) * 16 + i);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += v[q];
+      }
+      for (; b < gridDim.x; b += 16) t += __ldcg(partials + b * 16 + i);
+    }
     part[j][i] = t;
   }
   __syncthreads();
@@ -333,8 +345,8 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense,
 
 cudaError_t launch_conserved(int prec, const void* f, const Layout& L, const Model<double>& m, double* partials,
                              int max_blocks, unsigned* counter, double* result, unsigned* flags, cudaStream_t st) {
-  // about four rows per warp, at most max_blocks blocks
-  int b = blocks_for((long long)L.ny * L.nz, 4 * (RED_THREADS / 32));
+  // about sixteen rows per warp, at most max_blocks blocks
+  int b = blocks_for((long long)L.ny * L.nz, 16 * (RED_THREADS / 32));
   if (b > max_blocks) b = max_blocks;
   if (b < 1) b = 1;
   if (prec == LBM_FP64)
