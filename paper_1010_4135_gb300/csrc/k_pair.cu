@@ -1,8 +1,9 @@
 // Tiled single-precision fused step, two x-adjacent cells per thread.
 //
 // Same plane ring as step_tiled_kernel (one 4D TMA copy per z plane into an
-// mbarrier-tracked ring; see tma_ring.cuh), but each of the 128 threads of a
-// 32 x 8 tile owns the cell pair (x, x+1).  The pair is loaded with one
+// mbarrier-tracked ring; see tma_ring.cuh), but each thread of a TX x 8 tile
+// (PairGeo below; 32 x 8 and 128 threads by default) owns the cell pair
+// (x, x+1).  The pair is loaded with one
 // 64-bit shared load per field and neighbour row, and everything that is the
 // same arithmetic for both cells runs as packed f32x2 operations (FADD2,
 // FMUL2, FFMA2), which halves the instructions the schedulers issue.
