@@ -43,11 +43,11 @@ def parse():
     p.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serve: workspace budget (0 = 80%% of free)")
     p.add_argument("--l1-sample", type=float, default=0.0,
                    help="serve: fraction of requests (seeded) checked against the FP64 path (0 = the three smallest)")
-    p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "serve"],
+    p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "batch_small", "serve"],
                    help="droplet: 256^3 Mach-2 shock-droplet; bubble: 512x256x256 Mach-3 shock-bubble; "
                         "batch: the bubble grid plus 8 128^3 copies with seeded Mach numbers, one launch per "
-                        "step, replayed as a CUDA graph; serve: the seeded request stream through the "
-                        "continuous-batching server")
+                        "step, replayed as a CUDA graph; batch_small: the 8 128^3 copies alone (a profiling "
+                        "size); serve: the seeded request stream through the continuous-batching server")
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
     p.add_argument("--variant", default="tiled", choices=["tiled", "tiled64", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
     p.add_argument("--zchunk", type=int, default=0, help="z planes per CTA of the tiled kernel (0 = auto)")
@@ -63,16 +63,17 @@ def workload(name):
     return workloads.shock_bubble()
 
 
-def batch_workloads():
+def batch_workloads(small=False):
     """The 512x256x256 Mach-3 bubble and 8 128^3 bubbles whose Mach numbers
     are drawn (seed 4) uniformly in [1.5, 6]; (c1, c2, eta0, dt) of each from
     the von Neumann parameter rule (paper_1010_4135_gb300.stability) applied
     to the initial states and to the star states of the shock meeting the
-    bubble."""
+    bubble.  small: the eight 128^3 bubbles alone."""
     import workloads
     from paper_1010_4135_gb300 import stability
     out = []
-    for n, mach in [((512, 256, 256), 3.0)] + [((128, 128, 128), float(m)) for m in workloads.batch_machs(4, 8)]:
+    big = [] if small else [((512, 256, 256), 3.0)]
+    for n, mach in big + [((128, 128, 128), float(m)) for m in workloads.batch_machs(4, 8)]:
         r2, u2, p2, _ = workloads.rankine_hugoniot(mach)
         post, bubble = (r2, u2, 0.0, 0.0, p2 / r2), (0.1, 0.0, 0.0, 0.0, 10.0)
         states = [(1.0, 0.0, 0.0, 0.0, 1.0), post, bubble, *stability.interaction_states(post, bubble)]
@@ -84,12 +85,12 @@ def batch_workloads():
 
 
 def run_batch(args):
-    """One step = one batched launch advancing all nine grids; the timed steps
-    replay a captured CUDA graph of `graph_steps` steps."""
+    """One step = one batched launch advancing all grids of the batch; the
+    timed steps replay a captured CUDA graph of `graph_steps` steps."""
     import torch
     from paper_1010_4135_gb300 import sim as S
     torch.cuda.set_device(0)
-    ws = batch_workloads()
+    ws = batch_workloads(small=args.workload == "batch_small")
     sims = []
     for w in ws:
         s = S.from_workload(w, precision="fp32")
@@ -137,7 +138,7 @@ def run_batch(args):
                    "launch": f"one persistent batched step kernel per step, CUDA graph of {gsteps} steps",
                    "variant": tuned["variant"], "zchunk": tuned["zchunk"], "autotuned": args.zchunk == 0,
                    "tune_timings_ms": tuned.get("timings"),
-                   "l2": "no flush: 18 f buffers of 1.0-2.0 GB / 0.13 GB exceed the L2"},
+                   "l2": "no flush: the f buffers (0.13-2.0 GB each) exceed the L2 together"},
         "roofline": {"bound": "hbm", "achieved": alg / per_step / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": alg / per_step / 1e9 / peak, "peak_source": peak_kind,
                      "kernel": "step_pair_batch (all grids, one launch per step; time per step incl. graph gaps)",
@@ -527,7 +528,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
+    if args.workload in ("batch", "batch_small"):
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
