@@ -215,14 +215,19 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   }
 
   const float2 half = bc2(0.5f);
+  // F: the own pair of cell plane k; Fn: that of plane k+1, read as the z
+  // neighbour during plane k and kept in registers for the next plane
+  float2 F[NV], Fn[NV];
+  if (!timed_out) {
+    const float* Q0 = slot(0);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) F[i] = ld2(Q0 + i * PL + c);
+  }
   for (int k = 0; k < nzc && !timed_out; ++k) {
     const float* P0 = slot(k);
     const float* P1 = slot(k + 1);
     const float* P2 = slot(k + 2);
 
-    float2 F[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) F[i] = ld2(P0 + i * PL + c);
 
     // moments (relations e1-e3)
     const float2 sa = add(add(add(F[1], F[2]), add(F[3], F[4])), add(F[5], F[6]));
@@ -388,6 +393,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
       {
         const int sg = vsign(i, 2);
         const float2 Z1 = ld2(P1 + i * PL + c);
+        Fn[i] = Z1;
         const float2 H = h1[i];
         if (sg > 0) {
           const float2 D0 = sub(B, H);
@@ -481,6 +487,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     for (int i = 0; i < NV; ++i) {
       h2[i] = h1[i];
       h1[i] = F[i];
+      F[i] = Fn[i];
     }
     // ring plane k+3 (needed next step) must have landed; the barrier also
     // marks plane k as retired, so its slot takes plane k + NSLOT
