@@ -45,3 +45,29 @@ def test_served_results_equal_alone_and_budget_is_respected():
         assert np.array_equal(alone, j.rho), j.req
     st = serve.summary(done, srv.wall)
     assert st["p50_latency_s"] <= st["p99_latency_s"]
+
+
+def test_unhealthy_results_are_solved_again_with_the_next_parameters(monkeypatch):
+    """The health bits of every first attempt are forced to 'T <= 0' (on the
+    host, no GPU fault): each request is solved again with attempt 1's
+    parameters, and that result is bitwise the request solved alone with
+    them; latency keeps counting from the first arrival."""
+    from paper_1010_4135_gb300 import serve
+    from paper_1010_4135_gb300 import sim as S
+    real = serve.Server._health
+    monkeypatch.setattr(serve.Server, "_health",
+                        staticmethod(lambda job: 4 if job.attempt == 0 else real(job)))
+    tr = _trace()[:4]
+    srv = serve.Server(max_batch=4, tick=16, keep_results=True)
+    done = srv.run(tr)
+    assert len(done) == len(tr) and srv.retries == len(tr)
+    for j in done:
+        assert j.attempt == 1 and j.health == 0
+        assert j.params == serve.request_parameters(j.req, 1)
+        w = workloads.request_workload(j.req, *j.params)
+        s = S.from_workload(w, precision="fp32")
+        s.init(*w.initial_fields())
+        s.step(j.req["steps"])
+        alone, _, _ = s.moments()
+        assert np.array_equal(alone, j.rho)
+    assert serve.summary(done, srv.wall)["retried"] == len(tr)

@@ -82,3 +82,15 @@ def test_parameter_rule_sees_the_flow_behind_a_shocked_light_bubble():
     assert star[0][1] > 8.2
     c1, _, _, dt = S.choose_parameters([(1.0, 0.0, 0.0, 0.0, 1.0), post, bubble, *star], 1.0 / 128)
     assert c1 >= star[0][1] and dt is not None
+
+
+def test_request_parameter_candidates():
+    """Attempt 0 is the rule; attempt 1 lowers c1 by one (c2 = 3 c1, eta0 =
+    2 c1); attempt 2 keeps c1 and takes eta0 = c1."""
+    import workloads as W
+    from paper_1010_4135_gb300 import serve
+    req = {"id": 0, "grid": (64, 64, 64), "mach": 8.4, "ratio": 0.1, "steps": 10, "kind": "sphere"}
+    c1, c2, eta0, dt = serve.request_parameters(req)
+    assert (c2, eta0) == (3 * c1, 2 * c1)
+    assert serve.request_parameters(req, 1) == (c1 - 1, 3 * (c1 - 1), 2 * (c1 - 1), dt)
+    assert serve.request_parameters(req, 2) == (c1, c2, c1, dt)
