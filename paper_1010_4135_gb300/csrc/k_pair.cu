@@ -568,8 +568,15 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     const int chunk = (int)(local / per_chunk);
     const int t = (int)(local % per_chunk);
     const int z0 = chunk * it.zc;
-    pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, it.L, it.m, it.wt, it.rd, (t % it.tiles_x) * G::TX,
-                               (t / it.tiles_x) * G::TY, z0, min(it.zc, it.L.nz - z0), it.flags, smem, bars, jb,
+    // the unit's descriptors as locals: read through the runtime index e, the
+    // table's constants would otherwise be re-loaded at every use in the plane
+    // loop (256^3 alone: 0.497 -> 0.469 ms; eight 128^3: 0.556 -> 0.525 ms)
+    const Layout L = it.L;
+    const Model<float> m = it.m;
+    const WtDesc wt = it.wt;
+    const RecoverDesc rd = it.rd;
+    pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, L, m, wt, rd, (t % it.tiles_x) * G::TX,
+                               (t / it.tiles_x) * G::TY, z0, min(it.zc, L.nz - z0), it.flags, smem, bars, jb,
                                timed_out, tab.wait_limit);
   }
   if (threadIdx.x == 0) {

@@ -580,7 +580,10 @@ int run_steps(lbm_sim* s, int64_t n) {
   return LBM_OK;
 }
 
-constexpr int kBatchZchunk = 16;  // measured: 16 planes 0.527 ms, 32 planes 0.536 ms on 256^3
+// z planes per unit of the batched kernel when a sim has none set.  Measured
+// (GB300): eight 128^3 grids 0.526 / 0.522 / 0.529 ms per step at 16 / 24 / 32
+// planes; with the 512 x 256 x 256 grid added 1.430 / 1.394 / 1.386 ms.
+constexpr int kBatchZchunk = 24;
 
 int batch_check(lbm_sim* const* sims, int32_t n) {
   if (!sims || n < 1 || n > lbm::kMaxBatch) return LBM_EINVAL;
