@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
     p.add_argument("--variant", default="tiled", choices=["tiled", "tiled64", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
     p.add_argument("--zchunk", type=int, default=0, help="z planes per CTA of the tiled kernel (0 = auto)")
+    p.add_argument("--ztail", type=int, default=0,
+                   help="with --zchunk: short chunks of this many planes end each tile column (0 = none)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -102,9 +104,10 @@ def run_batch(args):
     if args.zchunk == 0:
         tuned = autotune.tune_batch(sims)
     else:
-        tuned = {"variant": args.variant if args.variant in ("tiled", "tiled64") else "tiled", "zchunk": args.zchunk}
+        tuned = {"variant": args.variant if args.variant in ("tiled", "tiled64") else "tiled", "zchunk": args.zchunk,
+                 "ztail": args.ztail}
     for s in sims:
-        s.set_launch(tuned["variant"], tuned["zchunk"])
+        s.set_launch(tuned["variant"], tuned["zchunk"], tuned["ztail"])
     S.step_batch(sims, max(2, args.warmup))
     gsteps = 10 if args.steps % 10 == 0 else 2
     steps = max(gsteps, args.steps - args.steps % gsteps)
@@ -136,7 +139,8 @@ def run_batch(args):
         "config": {"workload": "batch: " + ", ".join(w.name for w in ws), "cells": cells,
                    "c1_c2_eta0_dt": [[w.c1, w.c2, w.eta0, w.dt] for w in ws],
                    "launch": f"one persistent batched step kernel per step, CUDA graph of {gsteps} steps",
-                   "variant": tuned["variant"], "zchunk": tuned["zchunk"], "autotuned": args.zchunk == 0,
+                   "variant": tuned["variant"], "zchunk": tuned["zchunk"], "ztail": tuned["ztail"],
+                   "autotuned": args.zchunk == 0,
                    "tune_timings_ms": tuned.get("timings"),
                    "l2": "no flush: the f buffers (0.13-2.0 GB each) exceed the L2 together"},
         "roofline": {"bound": "hbm", "achieved": alg / per_step / 1e9, "peak": peak, "unit": "GB/s",
@@ -351,7 +355,7 @@ def run_ours(args):
     w = workload(args.workload)
     rho, u, T = w.initial_fields()
     s = S.from_workload(w, precision=args.precision)
-    s.set_launch(args.variant, args.zchunk)
+    s.set_launch(args.variant, args.zchunk, args.ztail)
     s.init(rho, u, T)
     tuned = None
     if args.precision == "fp32" and args.variant in ("tiled", "tiled64") and args.zchunk == 0:
@@ -452,6 +456,7 @@ def run_ours(args):
         "config": {**describe(w, args.precision),
                    "launch": {"variant": s.launch[0] if args.precision == "fp32" else "plain",
                               "zchunk": s.launch[1] if args.precision == "fp32" else None,
+                              "ztail": s.launch[2] if args.precision == "fp32" else None,
                               "autotuned": tuned is not None,
                               "tune_timings_ms": tuned.get("timings") if tuned else None}},
         "roofline": roofline,

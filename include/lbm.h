@@ -131,10 +131,16 @@ LBM_API int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, d
 LBM_API int lbm_set_scheme(lbm_sim* sim, int32_t scheme, int32_t dissipation);
 
 /* Launch configuration of the FP32 step kernel (the autotuner's knobs):
- * a LBM_VARIANT_* value; zchunk = z planes per CTA of the tiled kernels,
- * 0 = automatic.  All variants compute the same update (to float rounding);
- * FP64 sims always use the plain kernel. */
-LBM_API int lbm_set_launch(lbm_sim* sim, int32_t variant, int32_t zchunk);
+ * a LBM_VARIANT_* value; zchunk = z planes per CTA (one unit of work) of the
+ * tiled kernels, 0 = automatic; ztail (pair kernels: TILED, TILED_FILL,
+ * TILED64 and lbm_step_batch) = 0 for equal chunks, or a length below zchunk:
+ * the first floor((nz - ztail) / zchunk) chunks of each tile column have
+ * zchunk planes and the rest of the column is split into chunks of ztail
+ * planes, launched last, so that the SMs run out of work together.  All
+ * variants and chunkings compute the same update (the pair kernels bitwise;
+ * the others to float rounding); FP64 sims always use the plain kernel.
+ * LBM_EINVAL for an unknown variant or a negative zchunk or ztail. */
+LBM_API int lbm_set_launch(lbm_sim* sim, int32_t variant, int32_t zchunk, int32_t ztail);
 
 /* FP64 temperature recovery of the FP32 tiled step (LBM_VARIANT_TILED and
  * lbm_step_batch).  The FP32 T = (E/rho - u^2)/b of Sec. 2 subtracts large

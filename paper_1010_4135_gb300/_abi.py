@@ -46,7 +46,7 @@ SIGNATURES = [
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int32, _vp, ctypes.c_size_t, _vp,
                                   ctypes.POINTER(_vp)]),
     ("lbm_set_scheme", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
-    ("lbm_set_launch", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    ("lbm_set_launch", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("lbm_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint32]),
     ("lbm_set_t_recovery", ctypes.c_int, [_vp, ctypes.c_double]),
     ("lbm_init", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int32]),

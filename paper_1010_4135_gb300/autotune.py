@@ -1,11 +1,13 @@
 """Launch-configuration autotuner of the FP32 step.
 
 The knobs are the tile shape of the pair kernel ("tiled": 32 x 8 tiles, two
-CTAs of 4 warps per SM; "tiled64": 64 x 8 tiles, one CTA of 8 warps per SM)
-and its z chunk (planes one CTA marches): long chunks
-re-read fewer boundary planes, short chunks fill the SMs and balance the
-tail.  The best pair depends on the grid's shape and the SM count, so it is
-measured: each candidate runs a few steps of the sim's own
+CTAs of 4 warps per SM; "tiled64": 64 x 8 tiles, one CTA of 8 warps per SM),
+its z chunk (planes one CTA marches) and the tail chunk: long chunks re-read
+fewer boundary planes and pay fewer unit prologues, short chunks fill the SMs;
+a tail of short chunks at the end of each column (launched last) lets the SMs
+run out of work together (256^3 on GB300: 0.474 ms per step with 24-plane
+chunks, 0.464 ms with 32-plane chunks ending in 8-plane ones).  The best
+choice depends on the grid's shape and the SM count, so it is measured: each candidate runs a few steps of the sim's own
 state on a scratch copy of the sim (its own workspace, so the user's state
 and step count are untouched), timed with CUDA events on the scratch sim's
 stream; the fastest is applied and cached per (device, grid, precision,
@@ -22,6 +24,7 @@ import threading
 import torch
 
 ZCHUNKS = (4, 8, 12, 16, 24, 32, 48)
+ZTAILS = (0, 8, 16)  # 0: equal chunks; a tail length is tried only below the chunk length
 VARIANTS = ("tiled", "tiled64")
 _lock = threading.Lock()
 
@@ -52,13 +55,13 @@ def _store(path, key, value):
 
 def key_of(sims, batched: bool, device_name: str | None = None, sms: int | None = None,
            variants=None) -> str:
-    """Cache key: device, SM count, the candidate tile shapes, and per sim the
-    grid, precision, scheme and boundary kinds."""
+    """Cache key: device, SM count, the candidate tile shapes and tail lengths,
+    and per sim the grid, precision, scheme and boundary kinds."""
     if device_name is None or sms is None:
         props = torch.cuda.get_device_properties(sims[0].device)
         device_name, sms = props.name, props.multi_processor_count
     parts = [device_name.replace(" ", "_"), str(int(sms)), "batch" if batched else "single",
-             ",".join(variants or VARIANTS)]
+             ",".join(variants or VARIANTS), "tails" + ",".join(str(t) for t in ZTAILS)]
     for s in sims:
         c = s.config
         parts.append("x".join(str(int(v)) for v in (c["nx"], c["ny"], c["nz"])) + f":{c['precision']}:{c['scheme']}:"
@@ -76,9 +79,15 @@ def _time(run, steps: int, warmup: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
+def candidates(zchunks=ZCHUNKS, variants=VARIANTS) -> list:
+    """(variant, zchunk, ztail) launches to measure: every tile shape and z
+    chunk with equal chunks, and with each tail length below the chunk."""
+    return [(v, int(zc), int(zt)) for v in variants for zc in zchunks for zt in ZTAILS if not zt or zt < zc]
+
+
 def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bool = False,
             variants=VARIANTS) -> dict:
-    """{(variant, zchunk): ms per step} of the given sims' current states on scratch copies."""
+    """{(variant, zchunk, ztail): ms per step} of the given sims' current states on scratch copies."""
     from . import sim as S
     scratch = []
     try:
@@ -91,16 +100,15 @@ def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bo
                 c = s.clone(stream=torch.cuda.current_stream(s.device))
                 scratch.append((c, f))
             out = {}
-            for v in variants:
-                for zc in zchunks:
-                    for c, f in scratch:
-                        c.set_launch(v, zc)
-                        c.set_f(f)
-                    if batched:
-                        run = lambda n: S.step_batch([c for c, _ in scratch], n)
-                    else:
-                        run = scratch[0][0].step
-                    out[(v, int(zc))] = _time(run, steps, warmup)
+            for v, zc, zt in candidates(zchunks, variants):
+                for c, f in scratch:
+                    c.set_launch(v, zc, zt)
+                    c.set_f(f)
+                if batched:
+                    run = lambda n: S.step_batch([c for c, _ in scratch], n)
+                else:
+                    run = scratch[0][0].step
+                out[(v, zc, zt)] = _time(run, steps, warmup)
             return out
     finally:
         for c, _ in scratch:
@@ -109,32 +117,32 @@ def measure(sims, zchunks=ZCHUNKS, steps: int = 10, warmup: int = 2, batched: bo
 
 def tune(sim, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None,
          variants=VARIANTS) -> dict:
-    """Choose and apply the tile shape and z chunk of one FP32 sim; returns
-    {"variant", "zchunk", "ms", "cached", "timings"}."""
+    """Choose and apply the tile shape, z chunk and tail of one FP32 sim;
+    returns {"variant", "zchunk", "ztail", "ms", "cached", "timings"}."""
     return _tune([sim], zchunks, steps, use_cache, path, batched=False, variants=variants)
 
 
 def tune_batch(sims, zchunks=ZCHUNKS, steps: int = 10, use_cache: bool = True, path: str | None = None,
                variants=VARIANTS) -> dict:
-    """Choose and apply one tile shape and z chunk for sims stepped together (lbm_step_batch)."""
+    """Choose and apply one tile shape, z chunk and tail for sims stepped together (lbm_step_batch)."""
     return _tune(list(sims), zchunks, steps, use_cache, path, batched=True, variants=variants)
 
 
 def _tune(sims, zchunks, steps, use_cache, path, batched, key=None, variants=VARIANTS):
     if any(s.config["precision"] not in ("fp32", 1) for s in sims):
-        return {"variant": None, "zchunk": None, "ms": None, "cached": False, "timings": {}}
+        return {"variant": None, "zchunk": None, "ztail": None, "ms": None, "cached": False, "timings": {}}
     path = path or cache_path()
     key = key or key_of(sims, batched, variants=variants)
     hit = _load(path).get(key) if use_cache else None
     if hit is not None:
         for s in sims:
-            s.set_launch(hit["variant"], int(hit["zchunk"]))
+            s.set_launch(hit["variant"], int(hit["zchunk"]), int(hit.get("ztail", 0)))
         return {**hit, "cached": True}
     timings = measure(sims, zchunks, steps, batched=batched, variants=variants)
     best = min(timings, key=timings.get)
     for s in sims:
         s.set_launch(*best)
-    rec = {"variant": best[0], "zchunk": best[1], "ms": timings[best],
-           "timings": {f"{v}:{z}": t for (v, z), t in timings.items()}}
+    rec = {"variant": best[0], "zchunk": best[1], "ztail": best[2], "ms": timings[best],
+           "timings": {f"{v}:{z}:{t}": ms for (v, z, t), ms in timings.items()}}
     _store(path, key, rec)
     return {**rec, "cached": False}

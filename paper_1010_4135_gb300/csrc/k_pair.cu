@@ -517,7 +517,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
 template <int SCHEME, bool WT, class G>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_kernel(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
-                     Layout L, Model<float> m, WtDesc wt, RecoverDesc rd, int zc, unsigned* __restrict__ flags,
+                     Layout L, Model<float> m, WtDesc wt, RecoverDesc rd, ZSched zs, unsigned* __restrict__ flags,
                      unsigned wait_limit) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + G::NSLOT * G::SLOT_STRIDE);
@@ -527,11 +527,10 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int z0 = blockIdx.z * zc;
   unsigned jb = 0;
   bool timed_out = false;
-  pair_unit<SCHEME, WT, G>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY, z0,
-                           min(zc, L.nz - z0), flags, smem, bars, jb, timed_out, wait_limit);
+  pair_unit<SCHEME, WT, G>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY,
+                           zs.z0(blockIdx.z), zs.len(blockIdx.z, L.nz), flags, smem, bars, jb, timed_out, wait_limit);
 }
 
 // Persistent batched step: two CTAs per SM take the units of every grid in
@@ -567,7 +566,6 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     const long long per_chunk = (long long)it.tiles_x * it.tiles_y;
     const int chunk = (int)(local / per_chunk);
     const int t = (int)(local % per_chunk);
-    const int z0 = chunk * it.zc;
     // the unit's descriptors as locals: read through the runtime index e, the
     // table's constants would otherwise be re-loaded at every use in the plane
     // loop (256^3 alone: 0.497 -> 0.469 ms; eight 128^3: 0.556 -> 0.525 ms)
@@ -575,9 +573,10 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     const Model<float> m = it.m;
     const WtDesc wt = it.wt;
     const RecoverDesc rd = it.rd;
+    const ZSched zs = it.zs;
     pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, L, m, wt, rd, (t % it.tiles_x) * G::TX,
-                               (t / it.tiles_x) * G::TY, z0, min(it.zc, L.nz - z0), it.flags, smem, bars, jb,
-                               timed_out, tab.wait_limit);
+                               (t / it.tiles_x) * G::TY, zs.z0(chunk), zs.len(chunk, L.nz), it.flags, smem, bars,
+                               jb, timed_out, tab.wait_limit);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -604,28 +603,28 @@ cudaError_t set_attributes() {
 
 template <int SCHEME, class G>
 cudaError_t launch_scheme(const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                          const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
-                          unsigned wait_limit, cudaStream_t st) {
-  dim3 grid((L.nx + G::TX - 1) / G::TX, (L.ny + G::TY - 1) / G::TY, (L.nz + zc - 1) / zc);
+                          const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
+                          unsigned* flags, unsigned wait_limit, cudaStream_t st) {
+  dim3 grid((L.nx + G::TX - 1) / G::TX, (L.ny + G::TY - 1) / G::TY, zs.nch);
   const bool any = wt.per[0] || wt.per[1] || wt.per[2] || wt.xlo || wt.xhi;
   if (any)
-    step_pair_kernel<SCHEME, true, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zc, flags,
+    step_pair_kernel<SCHEME, true, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs, flags,
                                                                          wait_limit);
   else
-    step_pair_kernel<SCHEME, false, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zc, flags,
+    step_pair_kernel<SCHEME, false, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs, flags,
                                                                           wait_limit);
   return cudaGetLastError();
 }
 
 template <class G>
 cudaError_t launch_geo(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
-                       const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc, unsigned* flags,
-                       unsigned wait_limit, cudaStream_t st) {
+                       const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
+                       unsigned* flags, unsigned wait_limit, cudaStream_t st) {
   switch (scheme) {
-    case LBM_SCHEME_NND: return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+    case LBM_SCHEME_NND: return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
     case LBM_SCHEME_UPWIND2:
-      return launch_scheme<LBM_SCHEME_UPWIND2, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
-    default: return launch_scheme<LBM_SCHEME_UPWIND1, G>(map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+      return launch_scheme<LBM_SCHEME_UPWIND2, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
+    default: return launch_scheme<LBM_SCHEME_UPWIND1, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
   }
 }
 
@@ -668,10 +667,10 @@ cudaError_t launch_step_pair_batch(int cols, int scheme, const BatchTable& tab, 
 }
 
 cudaError_t launch_step_pair(int cols, int scheme, const CUtensorMap& map, const float* fin, float* fout,
-                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc,
-                             unsigned* flags, unsigned wait_limit, cudaStream_t st) {
-  if (cols == 64) return launch_geo<Geo64>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
-  return launch_geo<Geo32>(scheme, map, fin, fout, L, m, wt, rd, zc, flags, wait_limit, st);
+                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd,
+                             const ZSched& zs, unsigned* flags, unsigned wait_limit, cudaStream_t st) {
+  if (cols == 64) return launch_geo<Geo64>(scheme, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
+  return launch_geo<Geo32>(scheme, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
 }
 
 }  // namespace lbm

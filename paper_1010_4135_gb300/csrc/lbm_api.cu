@@ -160,7 +160,8 @@ struct lbm_sim {
   int layers_ok[2];     // buffer b's non-FIXED boundary layers match its interior
   unsigned wait_limit;  // polls of a TMA data wait before the step kernel gives up
   int variant;          // LBM_VARIANT_* of the FP32 step
-  int zchunk;           // 0 = automatic
+  int zchunk;           // z planes per unit of the tiled kernels, 0 = automatic
+  int ztail;            // pair kernels: short chunks of ztail planes end the z range (0 = none)
   int num_sms;
   CUtensorMap tmap[2];  // FP32: TMA descriptors of the two f buffers, box 40 x 12 x 1 x 15 (32 x 8 tiles)
   CUtensorMap wmap[2];  // the same with box 72 x 12 x 1 x 15 (64 x 8 tiles, variant TILED64)
@@ -444,6 +445,7 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
   s->variant = LBM_VARIANT_TILED;
   s->wait_limit = 1u << 22;
   s->zchunk = 0;
+  s->ztail = 0;
   s->num_sms = 0;
   if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
       s->num_sms < 1) {
@@ -485,12 +487,13 @@ int lbm_set_scheme(lbm_sim* s, int32_t scheme, int32_t dissipation) {
   return LBM_OK;
 }
 
-int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk) {
+int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk, int32_t ztail) {
   if (!s) return LBM_EINVAL;
   if (s->failed) return LBM_ESTATE;
-  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED64 || zchunk < 0) return LBM_EINVAL;
+  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED64 || zchunk < 0 || ztail < 0) return LBM_EINVAL;
   s->variant = variant;
   s->zchunk = zchunk;
+  s->ztail = ztail;
   s->layers_ok[0] = s->layers_ok[1] = 0;
   return LBM_OK;
 }
@@ -563,7 +566,8 @@ int run_steps(lbm_sim* s, int64_t n) {
         const CUtensorMap& map = shape.tx == 64 ? s->wmap[s->cur] : s->tmap[s->cur];
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_pair(shape.tx, s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf, wt,
-                                         s->rd, zc, s->flags, s->wait_limit, s->st));
+                                         s->rd, lbm::make_zsched(s->L.nz, zc, s->ztail), s->flags, s->wait_limit,
+                                         s->st));
       } else {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf,
@@ -632,9 +636,9 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
       it.rd = s->rd;
       it.tiles_x = (s->L.nx + shape.tx - 1) / shape.tx;
       it.tiles_y = (s->L.ny + shape.ty - 1) / shape.ty;
-      it.zc = s->zchunk > 0 ? s->zchunk : kBatchZchunk;
+      it.zs = lbm::make_zsched(s->L.nz, s->zchunk > 0 ? s->zchunk : kBatchZchunk, s->ztail);
       it.first_unit = units;
-      units += (long long)it.tiles_x * it.tiles_y * ((s->L.nz + it.zc - 1) / it.zc);
+      units += (long long)it.tiles_x * it.tiles_y * it.zs.nch;
     }
     tab.n = n;
     tab.wait_limit = s0->wait_limit;

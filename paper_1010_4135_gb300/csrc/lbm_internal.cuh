@@ -219,13 +219,43 @@ struct PairShape {
   int tx, ty, bx, by, threads, ctas_per_sm;
 };
 PairShape pair_shape(int cols);
+
+// How the pair kernels split the z range of a tile column into chunks (one
+// chunk = one unit of work, a z-march of one CTA).  With zt = 0 all chunks
+// have zc planes.  With zt > 0 the first nbig = floor((nz - zt) / zc) chunks
+// have zc planes and the remaining planes are split into chunks of zt: the
+// short chunks come last in launch order, so the last units of a launch are
+// short and the SMs finish together.
+struct ZSched {
+  int zc, zt, nbig, nch;  // long and short chunk length, long chunks, all chunks
+  __host__ __device__ int z0(int c) const { return c < nbig ? c * zc : nbig * zc + (c - nbig) * zt; }
+  __host__ __device__ int len(int c, int nz) const {
+    const int l = c < nbig ? zc : zt;
+    return l < nz - z0(c) ? l : nz - z0(c);
+  }
+};
+// nz >= 1, zc >= 1; zt = 0, zt >= zc or zt >= nz: every chunk zc planes long
+inline ZSched make_zsched(int nz, int zc, int zt) {
+  ZSched z;
+  z.zc = zc;
+  if (zt <= 0 || zt >= zc || zt >= nz) {
+    z.zt = zc;
+    z.nch = z.nbig = (nz + zc - 1) / zc;
+  } else {
+    z.zt = zt;
+    z.nbig = (nz - zt) / zc;
+    z.nch = z.nbig + (nz - z.nbig * zc + zt - 1) / zt;
+  }
+  return z;
+}
+
 cudaError_t launch_step_pair(int cols, int scheme, const CUtensorMap& map, const float* fin, float* fout,
-                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, int zc,
-                             unsigned* flags, unsigned wait_limit, cudaStream_t st);
+                             const Layout& L, const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd,
+                             const ZSched& zs, unsigned* flags, unsigned wait_limit, cudaStream_t st);
 
 // Descriptor table of a batched step (passed by value as the kernel
 // parameter): one entry per grid, units [first_unit, first_unit +
-// tiles_x * tiles_y * ceil(nz / zc)) in z-chunk-major order.
+// tiles_x * tiles_y * zs.nch) in z-chunk-major order.
 constexpr int kMaxBatch = 48;
 struct BatchItem {
   const float* fin;
@@ -235,7 +265,8 @@ struct BatchItem {
   Model<float> m;
   WtDesc wt;
   RecoverDesc rd;
-  int tiles_x, tiles_y, zc;
+  ZSched zs;
+  int tiles_x, tiles_y;
   long long first_unit;
 };
 struct BatchTable {

@@ -37,7 +37,7 @@ class Sim:
         self._config = dict(nx=nx, ny=ny, nz=nz, c1=c1, c2=c2, eta0=eta0, tau=tau, dt=dt, dx=dx, gamma=gamma,
                             precision=precision, bc_lo=bc_lo, bc_hi=bc_hi, fixed_lo=fixed_lo, fixed_hi=fixed_hi,
                             scheme=scheme, dissipation=dissipation, device=device)
-        self.launch = ("tiled", 0)
+        self.launch = ("tiled", 0, 0)  # (variant, zchunk, ztail)
         self.shape = (int(nz), int(ny), int(nx))
         self.prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.dtype = np.float64 if self.prec == A.LBM_FP64 else np.float32
@@ -103,17 +103,18 @@ class Sim:
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         A.check(A.lbm_set_scheme(self._h, s, int(bool(dissipation))), "lbm_set_scheme")
 
-    def set_launch(self, variant="tiled", zchunk: int = 0):
+    def set_launch(self, variant="tiled", zchunk: int = 0, ztail: int = 0):
         """FP32 step kernel: "tiled" (32 x 8 TMA plane tiles, cell pairs, boundary layers
         written by the step; default), "tiled64" (the same on 64 x 8 tiles), "tiled_fill"
         (boundary layers by a fill launch), "tiled_single" (one cell per thread) or "plain";
-        zchunk = z planes per CTA (0 = auto)."""
+        zchunk = z planes per CTA (0 = auto); ztail > 0 (pair kernels): the end of each
+        tile column is split into short chunks of ztail planes, launched last."""
         v = {"tiled": A.LBM_VARIANT_TILED, "plain": A.LBM_VARIANT_PLAIN,
              "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL,
              "tiled64": A.LBM_VARIANT_TILED64}[variant] \
             if isinstance(variant, str) else int(variant)
-        A.check(A.lbm_set_launch(self._h, v, int(zchunk)), "lbm_set_launch")
-        self.launch = (variant, int(zchunk))
+        A.check(A.lbm_set_launch(self._h, v, int(zchunk), int(ztail)), "lbm_set_launch")
+        self.launch = (variant, int(zchunk), int(ztail))
 
     def init(self, rho, u, T):
         """f = f^eq(rho, u, T); arrays shaped [nz,ny,nx] / [3,nz,ny,nx] (numpy or CUDA tensors)."""

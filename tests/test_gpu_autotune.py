@@ -26,8 +26,9 @@ def test_tune_measures_applies_and_caches(tmp_path):
     before = a.get_f()
     path = str(tmp_path / "launch.json")
     r = autotune.tune(a, zchunks=(2, 4, 9), steps=4, path=path)
-    assert not r["cached"] and r["zchunk"] in (2, 4, 9) and len(r["timings"]) == 6
-    assert a.launch == (r["variant"], r["zchunk"]) and a.steps_done == 3
+    # chunks 2, 4, 9 with equal chunks, and 9 with a tail of 8: four launches per tile shape
+    assert not r["cached"] and r["zchunk"] in (2, 4, 9) and len(r["timings"]) == 8
+    assert a.launch == (r["variant"], r["zchunk"], r["ztail"]) and a.steps_done == 3
     assert np.array_equal(a.get_f(), before)
     a.step(5)
     b = sim_for(cfg, "fp32")
@@ -47,6 +48,6 @@ def test_tune_batch_applies_one_chunk_to_all(tmp_path):
         s.set_f(initial_f(cfg, seed=81 + k).astype(np.float32))
         sims.append(s)
     r = autotune.tune_batch(sims, zchunks=(3, 8), steps=4, path=str(tmp_path / "b.json"))
-    assert r["zchunk"] in (3, 8) and all(s.launch == (r["variant"], r["zchunk"]) for s in sims)
+    assert r["zchunk"] in (3, 8) and all(s.launch == (r["variant"], r["zchunk"], r["ztail"]) for s in sims)
     S.step_batch(sims, 2)
     assert all(s.health() == 0 for s in sims)

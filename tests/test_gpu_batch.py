@@ -32,9 +32,12 @@ def _mix_sims(seed):
     return cfgs, f0s, sims
 
 
-def test_batch_results_equal_alone():
+@pytest.mark.parametrize("zchunk,ztail", [(0, 0), (5, 2), (3, 1)])
+def test_batch_results_equal_alone(zchunk, ztail):
     from paper_1010_4135_gb300 import sim as S
     cfgs, f0s, sims = _mix_sims(40)
+    for s in sims:
+        s.set_launch("tiled", zchunk, ztail)
     S.step_batch(sims, 7)
     for c, f0, s in zip(cfgs, f0s, sims):
         alone = sim_for(c, "fp32")

@@ -80,9 +80,12 @@ def test_fp32_tiled_results_do_not_depend_on_z_chunking(variant):
     cfg = case_cfg("periodic_37x19x11")
     f0 = initial_f(cfg, seed=12).astype(np.float32)
     outs = []
-    for zc in (0, 1, 2, 3, 5, 11, 64):
+    # (z chunk, tail): equal chunks, and long chunks ending in short ones
+    # (nz = 11: (5, 2) -> 5 + 2 + 2 + 2, (8, 3) -> 8 + 3, (11, 4) -> 4 + 4 + 3)
+    for zc, zt in ((0, 0), (1, 0), (2, 0), (3, 0), (5, 0), (11, 0), (64, 0), (5, 2), (3, 1), (8, 3), (11, 4),
+                   (6, 5), (4, 9)):
         s = sim_for(cfg, "fp32")
-        s.set_launch(variant, zc)
+        s.set_launch(variant, zc, zt)
         s.set_f(f0)
         s.step(4)
         outs.append(s.get_f())
