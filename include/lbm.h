@@ -132,7 +132,8 @@ LBM_API int lbm_set_scheme(lbm_sim* sim, int32_t scheme, int32_t dissipation);
 
 /* Launch configuration of the FP32 step kernel (the autotuner's knobs):
  * a LBM_VARIANT_* value; zchunk = z planes per CTA (one unit of work) of the
- * tiled kernels, 0 = automatic; ztail (pair kernels: TILED, TILED_FILL,
+ * tiled kernels, 0 = automatic (chunk and tail chosen from the grid and the
+ * SM count; ztail is then ignored); ztail (pair kernels: TILED, TILED_FILL,
  * TILED64 and lbm_step_batch) = 0 for equal chunks, or a length below zchunk:
  * the first floor((nz - ztail) / zchunk) chunks of each tile column have
  * zchunk planes and the rest of the column is split into chunks of ztail

@@ -33,15 +33,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // Running sum of floats held as an unevaluated pair hi + lo (about 44
-// significant bits).  add() is exact up to the rounding of lo, which stays
-// of order 2^-24 |hi|, so n additions lose about n * 2^-48 relative.
+// significant bits).  add() keeps hi the rounded running sum and adds its
+// rounding error (exact, two_sum) to lo; renorm() folds lo back into hi
+// (|hi| >= |lo|, so the fast two-sum is exact) and is called every few adds,
+// so lo stays of order 2^-24 |hi| and n additions lose about n * 2^-48
+// relative.
 struct DFloat {
   float hi = 0.f, lo = 0.f;
   __device__ __forceinline__ void add(float x) {
     float s, e;
     two_sum(hi, x, s, e);
+    hi = s;
     lo += e;
-    two_sum(s, lo, hi, lo);  }
+  }
+  __device__ __forceinline__ void renorm() {
+    const float s = hi + lo;
+    lo = lo - (s - hi);
+    hi = s;
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -192,25 +201,42 @@ struct FieldAcc<double> {
     for (int i = 0; i < NV; ++i) s[i] = 0.0;
   }
   __device__ __forceinline__ void add(int i, double v) { s[i] += v; }
+  __device__ __forceinline__ void renorm() {}
   __device__ __forceinline__ double value(int i) const { return s[i]; }
 };
 template <>
 struct FieldAcc<float> {
   DFloat s[NV];
   __device__ __forceinline__ void add(int i, float v) { s[i].add(v); }
+  __device__ __forceinline__ void renorm() {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i].renorm();
+  }
   __device__ __forceinline__ double value(int i) const { return s[i].value(); }
 };
+
+// 16-byte vector loads of float / double rows (read once: streaming hint).
+__device__ __forceinline__ void load16(const float* p, float v[4]) {
+  const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load16(const double* p, double v[2]) {
+  const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+  v[0] = q.x; v[1] = q.y;
+}
 
 // Deterministic FP64 global sums of (rho, rho u, E) over interior cells.  The
 // moments are linear in f, so the kernel sums each field f_i over the cells
 // and combines the 15 field totals at the end: mass = sum_i F_i, momentum =
 // sum_i v_i F_i, energy = sum_i (v_i^2 + eta_i^2) F_i.  Each warp takes
-// whole x rows (global warp w: rows w, w + W, ...; lanes stride x by 32, so
-// every field load is a coalesced 128-byte line); warps reduce by a fixed
-// shuffle tree, blocks by warp order, and the last block to finish sums the
-// per-block totals with all its threads in a fixed split (16 strided
-// partial sums per field, then in order).  The order never depends on
-// timing, so the result is bitwise reproducible.
+// whole x rows (global warp w: rows w, w + W, ...); a lane reads 16 bytes of
+// each of the 15 fields per x step (a warp: 512 contiguous bytes per field),
+// all 15 loads issued before the first add, so enough bytes are in flight
+// to keep HBM busy; values past the row end are masked to zero.  Warps
+// reduce by a fixed shuffle tree, blocks by warp order, and the last block to
+// finish sums the per-block totals with all its threads in a fixed split (16
+// strided partial sums per field, then in order).  The order never depends
+// on timing, so the result is bitwise reproducible for a given grid.
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restrict__ f, Layout L, Model<double> m,
                                                                 double* __restrict__ partials,
@@ -226,15 +252,26 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nrows = L.ny * L.nz;
   const int nw = gridDim.x * WARPS;
+  constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte load
   for (int r = blockIdx.x * WARPS + warp; r < nrows; r += nw) {
-    const long long row = L.at(0, r % L.ny, r / L.ny);
-    for (int x = lane; x < L.nx; x += 32) {
+    // interior rows start at x = OX (a multiple of 8 elements): 16-byte aligned
+    const R* row = f + L.at(0, r % L.ny, r / L.ny);
+    for (int x0 = lane * VW; x0 < L.nx; x0 += 32 * VW) {
+      // the last vector may reach up to VW - 1 elements past the row end,
+      // into the row's halo and padding (inside the buffer); masked below
+      R v[NV][VW];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) load16(row + i * L.fs + x0, v[i]);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        const R v = f[i * L.fs + row + x];
-        bad |= !finite_value(v);
-        acc.add(i, v);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          const R e = x0 + k < L.nx ? v[i][k] : R(0);
+          bad |= !finite_value(e);
+          acc.add(i, e);
+        }
       }
+      acc.renorm();
     }
   }
   if (bad) atomicOr(flags, (unsigned)LBM_HEALTH_NONFINITE);
@@ -345,8 +382,8 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense,
 
 cudaError_t launch_conserved(int prec, const void* f, const Layout& L, const Model<double>& m, double* partials,
                              int max_blocks, unsigned* counter, double* result, unsigned* flags, cudaStream_t st) {
-  // about sixteen rows per warp, at most max_blocks blocks
-  int b = blocks_for((long long)L.ny * L.nz, 16 * (RED_THREADS / 32));
+  // about eight rows per warp, at most max_blocks blocks
+  int b = blocks_for((long long)L.ny * L.nz, 8 * (RED_THREADS / 32));
   if (b > max_blocks) b = max_blocks;
   if (b < 1) b = 1;
   if (prec == LBM_FP64)

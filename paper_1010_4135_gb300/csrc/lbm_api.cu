@@ -297,19 +297,23 @@ bool pair_variant(int variant) {
 int pair_cols(int variant) { return variant == LBM_VARIANT_TILED64 ? 64 : 32; }
 
 // z planes per CTA of the tiled kernels (`cols` x 8 tiles, `ctas` CTAs per
-// SM).  Each unit re-reads four planes around its chunk, so long chunks save
-// traffic; short chunks fill the SMs.  On 256^3 (GB300, 32 x 8 tiles) 16
-// planes measured best (0.519 ms; 8: 0.540, 32: 0.529, 52: 0.597): the
-// largest of 16, 12, 8, 6, 4 that still gives two waves.  The autotuner
-// (autotune.py) refines this per grid.
+// SM) when none is set: the largest of 32, 24, 16, 12, 8, 6, 4 that still
+// gives two waves of units.  Each unit re-reads four planes around its chunk
+// and pays a prologue, so long chunks save work; short chunks fill the SMs.
+// The pair kernels then end each column in 8-plane chunks (auto_ztail), so
+// the last wave is short.  Measured on GB300 (32 x 8 tiles): 256^3 gets 32 + 8
+// (0.464-0.469 ms; equal 16 / 24 / 32: 0.481 / 0.472 / 0.482), 192^3 32 + 8
+// (0.218; best measured 0.216), 128^3 12 + 8 (equal 12: 0.085).  The
+// autotuner (autotune.py) measures the choice per grid.
 int auto_zchunk(const Layout& L, int num_sms, int cols, int ctas) {
   const long long tiles = (long long)((L.nx + cols - 1) / cols) * ((L.ny + lbm::kTileY - 1) / lbm::kTileY);
   const long long want = 2LL * ctas * num_sms;
-  static const int cand[] = {16, 12, 8, 6, 4};
+  static const int cand[] = {32, 24, 16, 12, 8, 6, 4};
   for (int zc : cand)
     if (tiles * ((L.nz + zc - 1) / zc) >= want) return zc < L.nz ? zc : L.nz;
   return L.nz < 4 ? L.nz : 4;
 }
+int auto_ztail(int zc) { return zc >= 12 ? 8 : 0; }
 
 unsigned step_faces(const lbm_sim* s) {
   unsigned m = 0;
@@ -564,10 +568,10 @@ int run_steps(lbm_sim* s, int64_t n) {
                                            : auto_zchunk(s->L, s->num_sms, lbm::kTileX, 2));
       if (pair) {
         const CUtensorMap& map = shape.tx == 64 ? s->wmap[s->cur] : s->tmap[s->cur];
+        const lbm::ZSched zs = lbm::make_zsched(s->L.nz, zc, s->zchunk > 0 ? s->ztail : auto_ztail(zc));
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_pair(shape.tx, s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf, wt,
-                                         s->rd, lbm::make_zsched(s->L.nz, zc, s->ztail), s->flags, s->wait_limit,
-                                         s->st));
+                                         s->rd, zs, s->flags, s->wait_limit, s->st));
       } else {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf,
