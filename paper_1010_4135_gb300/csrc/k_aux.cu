@@ -182,7 +182,10 @@ __global__ void unpack_kernel(R* __restrict__ f, Layout L, const R* __restrict__
   for (int i = 0; i < NV; ++i) f[i * L.fs + idx] = dense[i * n + k];
 }
 
-constexpr int RED_THREADS = 256;
+// conservation sums: blocks of 12 warps, 4 row slots x 3 groups of 5 fields
+constexpr int RED_GROUPS = 3, RED_GF = NV / RED_GROUPS, RED_ROWS = 4;
+constexpr int RED_THREADS = 32 * RED_GROUPS * RED_ROWS;
+static_assert(RED_GROUPS * RED_GF == NV, "field groups cover the 15 fields");
 
 __device__ __forceinline__ bool finite_value(double v) { return fabs(v) < 1e300; }
 __device__ __forceinline__ bool finite_value(float v) { return fabsf(v) < 3.0e38f; }
@@ -191,26 +194,26 @@ __device__ __forceinline__ bool finite_value(float v) { return fabsf(v) < 3.0e38
 // for float storage an error-free double-float pair, converted to double at
 // the end (GB300's FP64 rate would make a per-value conversion and double
 // add the bottleneck of this memory-bound reduction).
-template <typename R>
+template <typename R, int N>
 struct FieldAcc;
-template <>
-struct FieldAcc<double> {
-  double s[NV];
+template <int N>
+struct FieldAcc<double, N> {
+  double s[N];
   __device__ FieldAcc() {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i] = 0.0;
+    for (int i = 0; i < N; ++i) s[i] = 0.0;
   }
   __device__ __forceinline__ void add(int i, double v) { s[i] += v; }
   __device__ __forceinline__ void renorm() {}
   __device__ __forceinline__ double value(int i) const { return s[i]; }
 };
-template <>
-struct FieldAcc<float> {
-  DFloat s[NV];
+template <int N>
+struct FieldAcc<float, N> {
+  DFloat s[N];
   __device__ __forceinline__ void add(int i, float v) { s[i].add(v); }
   __device__ __forceinline__ void renorm() {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) s[i].renorm();
+    for (int i = 0; i < N; ++i) s[i].renorm();
   }
   __device__ __forceinline__ double value(int i) const { return s[i].value(); }
 };
@@ -228,15 +231,17 @@ __device__ __forceinline__ void load16(const double* p, double v[2]) {
 // Deterministic FP64 global sums of (rho, rho u, E) over interior cells.  The
 // moments are linear in f, so the kernel sums each field f_i over the cells
 // and combines the 15 field totals at the end: mass = sum_i F_i, momentum =
-// sum_i v_i F_i, energy = sum_i (v_i^2 + eta_i^2) F_i.  Each warp takes
-// whole x rows (global warp w: rows w, w + W, ...); a lane reads 16 bytes of
-// each of the 15 fields per x step (a warp: 512 contiguous bytes per field),
-// all 15 loads issued before the first add, so enough bytes are in flight
-// to keep HBM busy; values past the row end are masked to zero.  Warps
-// reduce by a fixed shuffle tree, blocks by warp order, and the last block to
-// finish sums the per-block totals with all its threads in a fixed split (16
-// strided partial sums per field, then in order).  The order never depends
-// on timing, so the result is bitwise reproducible for a given grid.
+// sum_i v_i F_i, energy = sum_i (v_i^2 + eta_i^2) F_i.  Each warp takes whole
+// x rows (rows b * RED_ROWS + slot, stepping by gridDim.x * RED_ROWS) and one
+// group of five fields, three warps per row slot; a lane reads 16 bytes of
+// each of its five fields per x step (a warp: 512 contiguous bytes per
+// field), all five loads issued before the first add.  Few registers per
+// thread let many warps, and so many bytes, be in flight per SM.  Values
+// past the row end are masked to zero.  Warps reduce by a fixed shuffle
+// tree, blocks by warp order, and the last block to finish sums the
+// per-block totals with 256 of its threads in a fixed split (16 strided
+// partial sums per field, then in order).  The order never depends on
+// timing, so the result is bitwise reproducible for a given grid.
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restrict__ f, Layout L, Model<double> m,
                                                                 double* __restrict__ partials,
@@ -247,23 +252,25 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   __shared__ double wsum[WARPS][16];
   __shared__ double part[16][16];
   __shared__ bool last;
-  FieldAcc<R> acc;
+  FieldAcc<R, RED_GF> acc;
   bool bad = false;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = warp % RED_GROUPS, slot = warp / RED_GROUPS;
   const int nrows = L.ny * L.nz;
-  const int nw = gridDim.x * WARPS;
+  const int nr = gridDim.x * RED_ROWS;
   constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte load
-  for (int r = blockIdx.x * WARPS + warp; r < nrows; r += nw) {
+  const R* fg = f + (long long)grp * RED_GF * L.fs;
+  for (int r = blockIdx.x * RED_ROWS + slot; r < nrows; r += nr) {
     // interior rows start at x = OX (a multiple of 8 elements): 16-byte aligned
-    const R* row = f + L.at(0, r % L.ny, r / L.ny);
+    const R* row = fg + L.at(0, r % L.ny, r / L.ny);
     for (int x0 = lane * VW; x0 < L.nx; x0 += 32 * VW) {
       // the last vector may reach up to VW - 1 elements past the row end,
       // into the row's halo and padding (inside the buffer); masked below
-      R v[NV][VW];
+      R v[RED_GF][VW];
 #pragma unroll
-      for (int i = 0; i < NV; ++i) load16(row + i * L.fs + x0, v[i]);
+      for (int i = 0; i < RED_GF; ++i) load16(row + i * L.fs + x0, v[i]);
 #pragma unroll
-      for (int i = 0; i < NV; ++i) {
+      for (int i = 0; i < RED_GF; ++i) {
 #pragma unroll
         for (int k = 0; k < VW; ++k) {
           const R e = x0 + k < L.nx ? v[i][k] : R(0);
@@ -276,12 +283,14 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   }
   if (bad) atomicOr(flags, (unsigned)LBM_HEALTH_NONFINITE);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
+  for (int i = 0; i < RED_GF; ++i) {
     double v = acc.value(i);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) wsum[warp][i] = v;
+    if (lane == 0) wsum[warp][grp * RED_GF + i] = v;
   }
+  // the other groups' fields of this warp are zero (adding them is exact)
+  if (lane < NV && (lane < grp * RED_GF || lane >= (grp + 1) * RED_GF)) wsum[warp][lane] = 0.0;
   __syncthreads();
   if (threadIdx.x < NV) {
     double t = 0.0;
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(RED_THREADS) conserved_kernel(const R* __restr
   __syncthreads();
   if (!last) return;
   __threadfence();
-  {
+  if (threadIdx.x < 256) {
     // field i, strided part j of 16; the partials are read through L2 (the
     // other blocks' writes are ordered before their counter increments),
     // eight loads in flight per step of the fixed-order sum
@@ -382,8 +391,8 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense,
 
 cudaError_t launch_conserved(int prec, const void* f, const Layout& L, const Model<double>& m, double* partials,
                              int max_blocks, unsigned* counter, double* result, unsigned* flags, cudaStream_t st) {
-  // about eight rows per warp, at most max_blocks blocks
-  int b = blocks_for((long long)L.ny * L.nz, 8 * (RED_THREADS / 32));
+  // about eight rows per row slot, at most max_blocks blocks
+  int b = blocks_for((long long)L.ny * L.nz, 8 * RED_ROWS);
   if (b > max_blocks) b = max_blocks;
   if (b < 1) b = 1;
   if (prec == LBM_FP64)
