@@ -108,7 +108,7 @@ class Server:
     each admitted grid the launch configuration the autotuner measured for
     its shape (once per shape, then cached; `tune_shapes` does it ahead).
     One batched launch runs one kernel, so every grid keeps the default tile
-    shape and only its z chunk is tuned."""
+    shape and only its z chunk and tail are tuned."""
 
     VARIANT = ("tiled",)
 

@@ -125,3 +125,6 @@ def test_batch_and_graph_argument_checks():
     s32.step(1)                           # buffers swapped outside the graph
     with pytest.raises(A.LbmError):
         g.launch()
+    # launch configuration: unknown variant, negative z chunk or tail
+    for bad in ((99, 0, 0), (A.LBM_VARIANT_TILED, -1, 0), (A.LBM_VARIANT_TILED, 8, -1)):
+        assert A.lbm_set_launch(s32.handle, *bad) == A.LBM_EINVAL
