@@ -640,7 +640,7 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
       it.rd = s->rd;
       it.tiles_x = (s->L.nx + shape.tx - 1) / shape.tx;
       it.tiles_y = (s->L.ny + shape.ty - 1) / shape.ty;
-      it.zs = lbm::make_zsched(s->L.nz, s->zchunk > 0 ? s->zchunk : kBatchZchunk, s->ztail);
+      it.zs = s->zchunk > 0 ? lbm::make_zsched(s->L.nz, s->zchunk, s->ztail) : lbm::make_zsched(s->L.nz, kBatchZchunk, 0);
       it.first_unit = units;
       units += (long long)it.tiles_x * it.tiles_y * it.zs.nch;
     }
