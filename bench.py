@@ -190,17 +190,18 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(key="step_fp32"):
-    """Hash of the kernel's code: its source files without comments and blank
-    lines (a comment edit does not change what ncu measured)."""
+    """Hash of the kernel's code: the token sequence of its source files
+    without comments (a comment edit or a re-wrapped line does not change
+    what ncu measured)."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1010_4135_gb300", "csrc")
     for fn in KERNEL_SOURCES[key]:
         with open(os.path.join(csrc, fn)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        lines = [ln.split("//", 1)[0].rstrip() for ln in text.splitlines()]
+        code = "\n".join(ln.split("//", 1)[0] for ln in text.splitlines())
         h.update(fn.encode())
-        h.update("\n".join(ln for ln in lines if ln).encode())
+        h.update(" ".join(re.findall(r"\w+|[^\w\s]", code)).encode())
     return h.hexdigest()[:16]
 
 

@@ -621,7 +621,8 @@ cudaError_t launch_geo(int scheme, const CUtensorMap& map, const float* fin, flo
                        const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
                        unsigned* flags, unsigned wait_limit, cudaStream_t st) {
   switch (scheme) {
-    case LBM_SCHEME_NND: return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
+    case LBM_SCHEME_NND:
+      return launch_scheme<LBM_SCHEME_NND, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
     case LBM_SCHEME_UPWIND2:
       return launch_scheme<LBM_SCHEME_UPWIND2, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
     default: return launch_scheme<LBM_SCHEME_UPWIND1, G>(map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);

@@ -640,7 +640,8 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
       it.rd = s->rd;
       it.tiles_x = (s->L.nx + shape.tx - 1) / shape.tx;
       it.tiles_y = (s->L.ny + shape.ty - 1) / shape.ty;
-      it.zs = s->zchunk > 0 ? lbm::make_zsched(s->L.nz, s->zchunk, s->ztail) : lbm::make_zsched(s->L.nz, kBatchZchunk, 0);
+      it.zs = s->zchunk > 0 ? lbm::make_zsched(s->L.nz, s->zchunk, s->ztail)
+                            : lbm::make_zsched(s->L.nz, kBatchZchunk, 0);
       it.first_unit = units;
       units += (long long)it.tiles_x * it.tiles_y * it.zs.nch;
     }
@@ -817,7 +818,8 @@ int lbm_moments(lbm_sim* s, double* rho, double* u, double* T, int32_t on_device
     LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_moments(s->prec, s->fbuf[s->cur], s->L, s->md, rho, u, T, s->st));
   } else {
     double* stg = (double*)spare(s);
-    LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_moments(s->prec, s->fbuf[s->cur], s->L, s->md, stg, stg + n, stg + 4 * n, s->st));
+    LBM_LAUNCH(s, LBM_KERNEL_OTHER,
+               lbm::launch_moments(s->prec, s->fbuf[s->cur], s->L, s->md, stg, stg + n, stg + 4 * n, s->st));
     LBM_CK(s, cudaMemcpyAsync(rho, stg, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     LBM_CK(s, cudaMemcpyAsync(u, stg + n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     LBM_CK(s, cudaMemcpyAsync(T, stg + 4 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
