@@ -113,3 +113,22 @@ def test_null_handles_and_status_strings(A):
     for code in range(0, -7, -1):
         assert A.lbm_status_str(code).startswith(b"LBM_")
     assert b"unknown" in A.lbm_status_str(42)
+
+
+def test_no_cpu_fallback_without_a_device(monkeypatch):
+    """The product path refuses to run without a CUDA device instead of
+    falling back to anything on the host."""
+    import torch
+    from paper_1010_4135_gb300 import sim as S
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    with pytest.raises(RuntimeError, match="CUDA device"):
+        S.Sim(8, 8, 8, 2.0, 6.0, 4.0, 1e-4, 1e-4, 0.1, precision="fp32")
+
+
+def test_build_fails_loudly_without_nvcc(monkeypatch):
+    from paper_1010_4135_gb300 import build
+    monkeypatch.delenv("NVCC", raising=False)
+    monkeypatch.setattr(build.shutil, "which", lambda name: None)
+    monkeypatch.setattr(build.os.path, "exists", lambda p: False)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        build.nvcc()
