@@ -82,7 +82,7 @@ enum { LBM_HEALTH_NONFINITE = 1u, LBM_HEALTH_RHO = 2u, LBM_HEALTH_T = 4u, LBM_HE
  * step kernel also writes the periodic images and the extrapolated /
  * reflected x-face layers of the state it produces, so no fill launch is
  * needed between steps; TILED64 = the same on 64 x 8 tiles (one CTA of 8
- * warps per SM); TILED_FILL = the TILED kernel with all boundary layers left
+ * warps per SM, run as two halves of 4 warps with their own barriers); TILED_FILL = the TILED kernel with all boundary layers left
  * to a fill launch before each step; TILED_SINGLE = 32 x 8 tiles, one cell
  * per thread; PLAIN = one thread per cell reading global memory.
  * lbm_step_batch takes TILED or TILED64 sims (all the same). */

@@ -37,14 +37,20 @@ using ring::tma_prefetch_plane;
 // (its x / y neighbours), z+1 and z+2 while z+3 lands.  PF > 0 also asks the
 // TMA unit to bring ring plane j+PF into L2 when plane j is copied, which
 // keeps more DRAM reads in flight per SM than the ring alone.
-template <int TX_, int TY_, int PF_>
+template <int TX_, int TY_, int PF_, bool SPLIT_ = false>
 struct PairGeo {
   static constexpr int TX = TX_, TY = TY_, NSLOT = 4, PF = PF_;
+  // SPLIT: the CTA works as two independent halves of 128 threads (the left
+  // and right 32 x 8 cells), each with its own named barrier per plane; a
+  // slot is refilled by whichever half releases it second (release counters
+  // after the mbarriers), so one half can run a plane ahead of the other.
+  static constexpr bool SPLIT = SPLIT_;
   static constexpr int BX = TX + 2 * TMA_LEFT, BY = TY + 4;  // tile with its halo
   static constexpr int PL = BX * BY;                          // floats per field in one plane tile
   static constexpr int SLOT_BYTES = NV * PL * 4;              // bytes one TMA copy delivers
   static constexpr int SLOT_STRIDE = (SLOT_BYTES + 127) / 128 * 128;
-  static constexpr int SMEM = NSLOT * SLOT_STRIDE + NSLOT * 8;
+  // slots, then the mbarriers, then (SPLIT) the release counters and the issued-plane count
+  static constexpr int SMEM = NSLOT * SLOT_STRIDE + NSLOT * 8 + (SPLIT ? 64 : 0);
   static constexpr int PX = TX / 2;                           // threads along x
   static constexpr int THREADS = PX * TY;
   // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved
@@ -56,18 +62,21 @@ struct PairGeo {
                 "64-bit shared loads: a half warp (one 128-byte wavefront) reads one contiguous tile row");
   static_assert(BX * 4 % 16 == 0 && BX <= 256, "TMA box inner extent: a 16-byte multiple, at most 256");
   static_assert(TX % 32 == 0, "tile rows start on 32-byte sectors (OX is a multiple of 8)");
-  __device__ static int col(int tid) { return tid % PX; }
-  __device__ static int row(int tid) { return tid / PX; }
+  static_assert(!SPLIT || (PX == 32 && TY == 8), "split halves: 16 pairs x 8 rows of 128 threads each");
+  // SPLIT: thread t of half h = t / 128 owns pair column 16 h + t % 16 of row (t % 128) / 16
+  __device__ static int col(int tid) { return SPLIT ? (tid & 15) + 16 * (tid >> 7) : tid % PX; }
+  __device__ static int row(int tid) { return SPLIT ? (tid & 127) >> 4 : tid / PX; }
 };
 // 32 x 8 tiles (the single-cell tiled kernel's box, 40 x 12): two CTAs of 4
 // warps per SM, L2 prefetch two planes ahead (256^3: 0.475 ms per step, 0.488
 // without the prefetch).
 using Geo32 = PairGeo<ring::TX, ring::TY, 2>;
 // 64 x 8 tiles (box 72 x 12 x 1 x 15): one CTA of 8 warps per SM, 288-byte
-// row reads.  Its data movement alone (ring + stores, no arithmetic) is
-// faster (0.362 ms against 0.443 ms on 256^3), but with the arithmetic one
-// CTA per SM cannot hide its per-plane barrier: 0.549 ms per step.
-using Geo64 = PairGeo<64, 8, 2>;
+// row reads, run as two split halves.  Its data movement alone (ring +
+// stores, no arithmetic) is faster (0.362 ms against 0.443 ms on 256^3);
+// with the arithmetic it takes 0.511 ms (0.549 ms with one CTA-wide barrier
+// per plane), against 0.465 ms for two independent 32 x 8 CTAs per SM.
+using Geo64 = PairGeo<64, 8, 2, true>;
 static_assert(Geo32::BX == ring::BX && Geo32::BY == ring::BY, "Geo32 shares the tiled kernel's tensor map");
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
@@ -81,6 +90,20 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ float mmc(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 __device__ __forceinline__ float2 mmc2(float2 x, float2 d) {
   return make_float2(mmc(x.x, fminf(d.x, 0.f), fmaxf(d.x, 0.f)), mmc(x.y, fminf(d.y, 0.f), fmaxf(d.y, 0.f)));
+}
+
+// Named barrier `id` over 128 threads with an OR of v across them.
+__device__ __forceinline__ bool half_sync_or(unsigned id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)v), "r"(id)
+      : "memory");
+  return r != 0u;
 }
 
 __device__ __forceinline__ int wrapi(int k, int n) {
@@ -158,17 +181,22 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   const int nplanes = nzc + 2;
 
   // copy ring plane j (interior z0 + j, padded z0 + j + 2) into its slot
-  int issued = 0;  // thread 0 only
+  // (SPLIT: release counters and the count of issued planes follow the mbarriers)
+  unsigned* rel = reinterpret_cast<unsigned*>(bars + NSLOT);
+  int* issued_s = reinterpret_cast<int*>(rel + NSLOT);
+  int issued = 0;  // thread 0 only (without SPLIT)
   auto issue = [&](int j) {
     const unsigned g = jb + (unsigned)j;
     float* dst = reinterpret_cast<float*>(smem + (g % NSLOT) * G::SLOT_STRIDE);
     mbar_expect_tx(&bars[g % NSLOT], G::SLOT_BYTES);
     tma_load_plane(dst, tin, x0 + OX - TMA_LEFT, y0, z0 + j + 2, &bars[g % NSLOT]);
     if (G::PF > 0 && j + G::PF < nplanes) tma_prefetch_plane(tin, x0 + OX - TMA_LEFT, y0, z0 + j + G::PF + 2);
-    issued = j + 1;
+    if (G::SPLIT) atomicMax(issued_s, j + 1);
+    else issued = j + 1;
   };
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (G::SPLIT) *issued_s = 0;
     for (int j = 0; j < NSLOT && j < nplanes; ++j) issue(j);
   }
   auto slot = [&](int j) {
@@ -492,22 +520,44 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     // ring plane k+3 (needed next step) must have landed; the barrier also
     // marks plane k as retired, so its slot takes plane k + NSLOT
     const bool ok = (k + 3 < nplanes) ? arrived(k + 3) : true;
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
-      break;
-    }
-    if (tid == 0 && k + NSLOT < nplanes) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(k + NSLOT);
+    if (G::SPLIT) {
+      // this half is done with plane k; the second half to say so refills its slot
+      const unsigned hf = (unsigned)tid >> 7;
+      if (half_sync_or(1u + hf, !ok)) {
+        timed_out = true;
+        break;
+      }
+      if ((tid & 127) == 0) {
+        __threadfence_block();
+        const unsigned prev = atomicAdd(&rel[(jb + (unsigned)k) % NSLOT], 1u);
+        if ((prev & 1u) && k + NSLOT < nplanes) {
+          __threadfence_block();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(k + NSLOT);
+        }
+      }
+    } else {
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+      if (tid == 0 && k + NSLOT < nplanes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(k + NSLOT);
+      }
     }
   }
+  // SPLIT halves leave the loop on their own (a half that timed out stops
+  // releasing slots, so the other one's waits run out too): rejoin here
+  if (G::SPLIT) timed_out = __syncthreads_or(timed_out) != 0;
 
   if (tid == 0 && timed_out) atomicOr(flags, (unsigned)LBM_HEALTH_TIMEOUT);
   if (bad) atomicOr(flags, bad);
   if (timed_out) {
     // leave no copy in flight: the newest plane of each slot is waited for (bounded)
     if (tid == 0) {
-      for (int j = max(0, issued - NSLOT); j < issued; ++j) drained(j);
+      const int n_issued = G::SPLIT ? *issued_s : issued;
+      for (int j = max(0, n_issued - NSLOT); j < n_issued; ++j) drained(j);
     }
     __syncthreads();
   }
@@ -524,6 +574,10 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < G::NSLOT; ++s) mbar_init(&bars[s], 1);
+    if (G::SPLIT) {
+      unsigned* rel = reinterpret_cast<unsigned*>(bars + G::NSLOT);
+      for (int s = 0; s < G::NSLOT; ++s) rel[s] = 0u;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -547,6 +601,10 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < G::NSLOT; ++s) mbar_init(&bars[s], 1);
+    if (G::SPLIT) {
+      unsigned* rel = reinterpret_cast<unsigned*>(bars + G::NSLOT);
+      for (int s = 0; s < G::NSLOT; ++s) rel[s] = 0u;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
