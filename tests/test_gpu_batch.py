@@ -32,12 +32,15 @@ def _mix_sims(seed):
     return cfgs, f0s, sims
 
 
-@pytest.mark.parametrize("zchunk,ztail", [(0, 0), (5, 2), (3, 1)])
-def test_batch_results_equal_alone(zchunk, ztail):
+@pytest.mark.parametrize("variant,zchunk,ztail", [("tiled", 0, 0), ("tiled", 5, 2), ("tiled", 3, 1),
+                                                  ("tiled64", 0, 0), ("tiled64", 4, 3)])
+def test_batch_results_equal_alone(variant, zchunk, ztail):
+    """Batched (any tile shape and chunking) equals each grid stepped alone
+    with the default launch: bitwise."""
     from paper_1010_4135_gb300 import sim as S
     cfgs, f0s, sims = _mix_sims(40)
     for s in sims:
-        s.set_launch("tiled", zchunk, ztail)
+        s.set_launch(variant, zchunk, ztail)
     S.step_batch(sims, 7)
     for c, f0, s in zip(cfgs, f0s, sims):
         alone = sim_for(c, "fp32")
