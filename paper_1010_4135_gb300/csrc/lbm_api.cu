@@ -9,6 +9,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "lbm_internal.cuh"
+#include "tma_ring.cuh"
 
 using lbm::Layout;
 using lbm::Model;
@@ -283,7 +284,7 @@ bool make_tmap(CUtensorMap* map, void* base, const Layout& L, int bx, int by) {
   const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)lbm::NV};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_SWIZZLE_NONE, lbm::ring::kPlaneL2Promotion,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
