@@ -224,7 +224,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   }
 
   unsigned bad = 0u;
-  // ring planes 0 .. 2 must have landed; the verdict is made uniform by the barrier
+  // ring planes 0 .. 2 must have landed; the outcome is made uniform by the barrier
   {
     bool ok = true;
     for (int j = 0; j < 3; ++j) ok = arrived(j) && ok;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(TX* TY, 2)
     for (int j = 0; j < NSLOT && j < nplanes; ++j) issue(j);
   }
   auto slot = [&](int j) { return reinterpret_cast<const float*>(smem + (j % NSLOT) * SLOT_STRIDE); };
-  // all threads poll (bounded); the verdict is made uniform by the barrier
+  // all threads poll (bounded); the outcome is made uniform by the barrier
   auto landed = [&](int j) {
     const bool ok = mbar_wait(&bars[j % NSLOT], (unsigned)((j / NSLOT) & 1));
     return __syncthreads_or(!ok) == 0;
