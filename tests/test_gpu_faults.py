@@ -26,11 +26,13 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def test_wait_that_runs_out_reports_timeout_and_device_stays_usable():
+@pytest.mark.parametrize("variant", ["tiled", "tiled64"])
+def test_wait_that_runs_out_reports_timeout_and_device_stays_usable(variant):
     from paper_1010_4135_gb300 import _abi as A
     cfg = case_cfg("periodic_37x19x11")
     f0 = initial_f(cfg, seed=70).astype(np.float32)
     s = sim_for(cfg, "fp32")
+    s.set_launch(variant)
     s.set_f(f0)
     A.check(A.lbm_set_wait_limit(s.handle, 0), "lbm_set_wait_limit")
     s.step(1)
@@ -43,6 +45,7 @@ def test_wait_that_runs_out_reports_timeout_and_device_stays_usable():
     s.step(3)
     assert s.health() == 0
     ref = sim_for(cfg, "fp32")
+    ref.set_launch(variant)
     ref.set_f(f0)
     ref.step(3)
     assert np.array_equal(s.get_f(), ref.get_f())
