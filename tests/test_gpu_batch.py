@@ -131,3 +131,26 @@ def test_batch_and_graph_argument_checks():
     # launch configuration: unknown variant, negative z chunk or tail
     for bad in ((99, 0, 0), (A.LBM_VARIANT_TILED, -1, 0), (A.LBM_VARIANT_TILED, 8, -1)):
         assert A.lbm_set_launch(s32.handle, *bad) == A.LBM_EINVAL
+
+
+def test_full_descriptor_table_and_one_more():
+    """LBM_MAX_BATCH (48) grids of mixed small shapes in one launch equal
+    their runs alone; a 49th grid is rejected."""
+    from paper_1010_4135_gb300 import _abi as A
+    from paper_1010_4135_gb300 import sim as S
+    names = ["periodic_37x19x11", "fixed_extrap_reflect_33x17x9", "reflect_extrap_fixed_20x12x14", "column_1x5x3"]
+    cfgs = [case_cfg(names[k % len(names)]) for k in range(A.LBM_MAX_BATCH + 1)]
+    sims, f0s = [], []
+    for k, c in enumerate(cfgs):
+        s = sim_for(c, "fp32")
+        f0 = initial_f(c, seed=200 + k).astype(np.float32)
+        s.set_f(f0)
+        sims.append(s)
+        f0s.append(f0)
+    assert A.lbm_step_batch(S._handles(sims), len(sims), 1) == A.LBM_EINVAL
+    S.step_batch(sims[:A.LBM_MAX_BATCH], 3)
+    for k in (0, 1, 2, 3, A.LBM_MAX_BATCH - 1):
+        alone = sim_for(cfgs[k], "fp32")
+        alone.set_f(f0s[k])
+        alone.step(3)
+        assert np.array_equal(sims[k].get_f(), alone.get_f()), k
