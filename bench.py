@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--requests", type=int, default=200, help="serve: number of requests in the trace")
     p.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     p.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serve: workspace budget (0 = 80%% of free)")
+    p.add_argument("--policy", default="fifo", choices=["fifo", "sjf"], help="serve: admission order")
     p.add_argument("--l1-sample", type=float, default=0.0,
                    help="serve: fraction of requests (seeded) checked against the FP64 path (0 = the three smallest)")
     p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "batch_small", "serve"],
@@ -485,7 +486,7 @@ def run_serve(args):
     torch.cuda.set_device(0)
     trace = workloads.serving_trace(seed=5, n=args.requests, rate=args.rate)
     budget = int(args.hbm_budget_gb * 2 ** 30) if args.hbm_budget_gb > 0 else None
-    srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True)
+    srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True, policy=args.policy)
     srv.tune_shapes(workloads.SERVING_GRIDS)  # before the trace starts: the server's grid menu
     done = srv.run(trace)
     stats = serve.summary(done, srv.wall)
@@ -517,7 +518,7 @@ def run_serve(args):
         "data": "synthetic",
         "config": {"workload": f"serving: {args.requests} requests, Poisson rate {args.rate}/s (seed 5), grids "
                                "64^3..256^3, Mach U[1.2,10], density ratio log-U[0.1,10], 500-3000 steps, FP32",
-                   "hbm_budget_bytes": srv.budget, "peak_resident_bytes": srv.peak_bytes,
+                   "admission": srv.policy, "hbm_budget_bytes": srv.budget, "peak_resident_bytes": srv.peak_bytes,
                    "peak_batch": srv.peak_batch, "host_seconds": dict(srv.host_s),
                    "l1_sample": (f"seeded {args.l1_sample:.0%} of the finished requests" if args.l1_sample > 0
                                  else "the three smallest finished requests")},

@@ -14,7 +14,11 @@ request that has run its steps gets its moments and health bits queued on
 the stream (lbm_moments_async / lbm_health_async into page-locked memory)
 and an event recorded behind them; its workspace is released once that
 event has completed, and its latency ends there (arrival to results on the
-host).  Waiting requests are admitted in arrival order.
+host).  Waiting requests are admitted in arrival order (policy "fifo", the
+default: a request that does not fit the memory left blocks the ones behind
+it), or shortest job first (policy "sjf": among the prepared requests that fit,
+the one with the fewest cell-updates; re-solves first), which cuts the
+median latency under overload at the cost of the largest requests.
 
 A request whose result comes back unhealthy (health bits: rho <= 0, T <= 0,
 non-finite) is solved again with the next parameter candidate
@@ -61,6 +65,32 @@ class Job:
 
 
 ATTEMPTS = 3  # parameter candidates per request
+POLICIES = ("fifo", "sjf")
+
+
+def work(req) -> int:
+    """Cell-updates a request needs."""
+    nx, ny, nz = req["grid"]
+    return int(nx) * int(ny) * int(nz) * int(req["steps"])
+
+
+def next_admission(waiting, used: int, budget: int, policy: str = "fifo"):
+    """The waiting job to admit next, or None: FIFO takes the head of the
+    queue if it is prepared and fits the memory left; SJF takes, among the
+    prepared jobs that fit, a re-solve first, else the one with the least
+    work (ties in arrival order)."""
+    if policy == "fifo":
+        if waiting and waiting[0].prep.done() and used + waiting[0].nbytes <= budget:
+            return waiting[0]
+        return None
+    best, key = None, None
+    for j in waiting:
+        if not j.prep.done() or used + j.nbytes > budget:
+            continue
+        k = (j.attempt == 0, work(j.req))
+        if key is None or k < key:
+            best, key = j, k
+    return best
 
 
 def request_parameters(req, attempt: int = 0):
@@ -113,7 +143,10 @@ class Server:
     VARIANT = ("tiled",)
 
     def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False, tune=True,
-                 prep_workers=2):
+                 prep_workers=2, policy="fifo"):
+        if policy not in POLICIES:
+            raise ValueError(f"policy must be one of {POLICIES}")
+        self.policy = policy
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(0.8 * free)
@@ -201,16 +234,20 @@ class Server:
                 while pending and pending[0]["arrival"] * time_scale <= clock():
                     r = pending.popleft()
                     waiting.append(Job(req=r, nbytes=workspace_bytes(r["grid"]), prep=pool.submit(prepare, r)))
-                # admission in arrival order, by footprint and batch slots, once prepared
-                while (waiting and waiting[0].prep.done() and len(active) < self.max_batch
-                       and used + waiting[0].nbytes <= self.budget):
-                    j = waiting.popleft()
+                # admission by the policy, footprint and batch slots, once prepared
+                while len(active) < self.max_batch:
+                    j = next_admission(waiting, used, self.budget, self.policy)
+                    if j is None:
+                        break
+                    waiting.remove(j)
                     self._admit(j)
                     j.admitted = clock()
                     used += j.nbytes
                     active.append(j)
-                if waiting and not active and not retiring and waiting[0].nbytes > self.budget:
-                    raise RuntimeError(f"request {waiting[0].req['id']} exceeds the HBM budget")
+                if waiting and not active and not retiring:
+                    big = next((j for j in waiting if j.nbytes > self.budget), None)
+                    if big is not None:
+                        raise RuntimeError(f"request {big.req['id']} exceeds the HBM budget")
                 self.host_s["admit"] += time.perf_counter() - h
                 self.peak_bytes = max(self.peak_bytes, used)
                 self.peak_batch = max(self.peak_batch, len(active))
@@ -266,7 +303,7 @@ class Server:
                 if retiring:
                     retiring[0].event.synchronize()
                 elif waiting:
-                    cf.wait([waiting[0].prep], timeout=0.05)
+                    cf.wait([j.prep for j in waiting], timeout=0.05, return_when=cf.FIRST_COMPLETED)
                 elif pending:
                     time.sleep(max(0.0, min(0.05, pending[0]["arrival"] * time_scale - clock())))
                 self.host_s["idle"] += time.perf_counter() - h

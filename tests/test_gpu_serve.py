@@ -22,13 +22,14 @@ def _trace():
     return tr
 
 
-def test_served_results_equal_alone_and_budget_is_respected():
+@pytest.mark.parametrize("policy", ["fifo", "sjf"])
+def test_served_results_equal_alone_and_budget_is_respected(policy):
     from paper_1010_4135_gb300 import serve
     from paper_1010_4135_gb300 import sim as S
     tr = _trace()
     sizes = [serve.workspace_bytes(r["grid"]) for r in tr]
     budget = 2 * max(sizes) + min(sizes)  # forces waiting for memory to free up
-    srv = serve.Server(hbm_budget=budget, max_batch=3, tick=16, keep_results=True)
+    srv = serve.Server(hbm_budget=budget, max_batch=3, tick=16, keep_results=True, policy=policy)
     done = srv.run(tr)
     assert len(done) == len(tr)
     assert srv.peak_bytes <= budget and srv.peak_batch <= 3
