@@ -50,7 +50,7 @@ def parse():
                         "step, replayed as a CUDA graph; batch_small: the 8 128^3 copies alone (a profiling "
                         "size); serve: the seeded request stream through the continuous-batching server")
     p.add_argument("--cpu-steps", type=int, default=3, help="oracle steps of the CPU baseline sample")
-    p.add_argument("--variant", default="tiled", choices=["tiled", "tiled64", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
+    p.add_argument("--variant", default="tiled", choices=["tiled", "tiled64", "split", "tiled_fill", "tiled_single", "plain"], help="FP32 step kernel")
     p.add_argument("--zchunk", type=int, default=0, help="z planes per CTA of the tiled kernel (0 = auto)")
     p.add_argument("--ztail", type=int, default=0,
                    help="with --zchunk: short chunks of this many planes end each tile column (0 = none)")

@@ -82,16 +82,23 @@ enum { LBM_HEALTH_NONFINITE = 1u, LBM_HEALTH_RHO = 2u, LBM_HEALTH_T = 4u, LBM_HE
  * step kernel also writes the periodic images and the extrapolated /
  * reflected x-face layers of the state it produces, so no fill launch is
  * needed between steps; TILED64 = the same on 64 x 8 tiles (one CTA of 8
- * warps per SM, run as two halves of 4 warps with their own barriers); TILED_FILL = the TILED kernel with all boundary layers left
- * to a fill launch before each step; TILED_SINGLE = 32 x 8 tiles, one cell
- * per thread; PLAIN = one thread per cell reading global memory.
- * lbm_step_batch takes TILED or TILED64 sims (all the same). */
+ * warps per SM, run as two halves of 4 warps with their own barriers);
+ * TILED_FILL = the TILED kernel with all boundary layers left to a fill
+ * launch before each step; TILED_SINGLE = 32 x 8 tiles, one cell per thread;
+ * PLAIN = one thread per cell reading global memory; TILED_SPLIT = the TILED
+ * tiles and ring with two warp groups per tile, one updating f_0..f_8 and the
+ * other f_9..f_14 of every cell pair (both form the moments), so each thread
+ * holds half the z-marching state and two CTAs of 8 warps fit on an SM; it
+ * writes the same boundary layers as TILED, and TILED, TILED64, TILED_FILL
+ * and TILED_SPLIT give bitwise the same results.  lbm_step_batch takes
+ * TILED, TILED64 or TILED_SPLIT sims (all the same). */
 enum {
   LBM_VARIANT_TILED = 0,
   LBM_VARIANT_PLAIN = 1,
   LBM_VARIANT_TILED_SINGLE = 2,
   LBM_VARIANT_TILED_FILL = 3,
-  LBM_VARIANT_TILED64 = 4
+  LBM_VARIANT_TILED64 = 4,
+  LBM_VARIANT_TILED_SPLIT = 5
 };
 
 /* Grid of nx*ny*nz interior cells of edge dx and the boundary kind of each

@@ -16,8 +16,8 @@ LBM_BC_PERIODIC, LBM_BC_FIXED, LBM_BC_EXTRAPOLATE, LBM_BC_REFLECT = 0, 1, 2, 3
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_SCHEME_NND, LBM_SCHEME_UPWIND2, LBM_SCHEME_UPWIND1 = 0, 1, 2
 LBM_HEALTH_NONFINITE, LBM_HEALTH_RHO, LBM_HEALTH_T, LBM_HEALTH_TIMEOUT = 1, 2, 4, 8
-LBM_VARIANT_TILED, LBM_VARIANT_PLAIN, LBM_VARIANT_TILED_SINGLE, LBM_VARIANT_TILED_FILL, LBM_VARIANT_TILED64 = \
-    0, 1, 2, 3, 4
+LBM_VARIANT_TILED, LBM_VARIANT_PLAIN, LBM_VARIANT_TILED_SINGLE, LBM_VARIANT_TILED_FILL, LBM_VARIANT_TILED64, \
+    LBM_VARIANT_TILED_SPLIT = 0, 1, 2, 3, 4, 5
 LBM_KERNEL_FILL, LBM_KERNEL_STEP, LBM_KERNEL_REDUCE, LBM_KERNEL_OTHER, LBM_NKERNEL = 0, 1, 2, 3, 4
 KERNEL_NAMES = ("fill", "step", "reduce", "other")
 LBM_MAX_BATCH = 48

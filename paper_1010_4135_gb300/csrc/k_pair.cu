@@ -21,6 +21,7 @@
 // even nx) columns, and the x-face layers of extrapolating or reflecting
 // faces (Sec. 4(2) rules applied to the two new boundary cells, which the
 // same thread holds), so the next step needs no separate fill for them.
+#include "pair_math.cuh"
 #include "tma_ring.cuh"
 
 namespace lbm {
@@ -79,18 +80,8 @@ using Geo32 = PairGeo<ring::TX, ring::TY, 2>;
 using Geo64 = PairGeo<64, 8, 2, true>;
 static_assert(Geo32::BX == ring::BX && Geo32::BY == ring::BY, "Geo32 shares the tiled kernel's tensor map");
 
-__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-
-// minmod(x, d) given lo = min(d, 0), hi = max(d, 0): exact.
-__device__ __forceinline__ float mmc(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
-__device__ __forceinline__ float2 mmc2(float2 x, float2 d) {
-  return make_float2(mmc(x.x, fminf(d.x, 0.f), fmaxf(d.x, 0.f)), mmc(x.y, fminf(d.y, 0.f), fmaxf(d.y, 0.f)));
-}
+using pm::bc2;
+using pm::ld2;
 
 // Named barrier `id` over 128 threads with an OR of v across them.
 __device__ __forceinline__ bool half_sync_or(unsigned id, bool v) {
@@ -104,58 +95,6 @@ __device__ __forceinline__ bool half_sync_or(unsigned id, bool v) {
       : "r"((unsigned)v), "r"(id)
       : "memory");
   return r != 0u;
-}
-
-__device__ __forceinline__ int wrapi(int k, int n) {
-  const int r = k % n;
-  return r < 0 ? r + n : r;
-}
-
-// rho, u, T of one cell from its 15 values (stride pl floats) in FP64
-// (relations e1-e3 summed in double); out of line, called only for cells
-// whose FP32 recovery is ill-conditioned (RecoverDesc).
-struct Macro1 {
-  float rho, ux, uy, uz, T;
-};
-__device__ __noinline__ Macro1 recover_fp64(const float* q, int pl, double c1, double s, double eta0sq,
-                                            double c1sq, double c2sq, double inv_b) {
-  double f[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) f[i] = (double)q[i * pl];
-  const double sa = ((f[1] + f[2]) + (f[3] + f[4])) + (f[5] + f[6]);
-  const double dpp = f[7] + f[8], dpm = f[9] + f[10], dmp = f[11] + f[12], dmm = f[13] + f[14];
-  const double sd = (dpp + dpm) + (dmp + dmm);
-  const double rho = f[0] + sa + sd;
-  const double mx = c1 * (f[1] - f[2]) + s * ((dpp + dpm) - (dmp + dmm));
-  const double my = c1 * (f[3] - f[4]) + s * ((dpp + dmp) - (dpm + dmm));
-  const double mz = c1 * (f[5] - f[6]) + s * (((f[7] + f[9]) + (f[11] + f[13])) - ((f[8] + f[10]) + (f[12] + f[14])));
-  const double E = eta0sq * f[0] + c1sq * sa + c2sq * sd;
-  const double ux = mx / rho, uy = my / rho, uz = mz / rho;
-  const double T = (E / rho - (ux * ux + uy * uy + uz * uz)) * inv_b;
-  return {(float)rho, (float)ux, (float)uy, (float)uz, (float)T};
-}
-
-// The two layers outside an x face from the boundary cell c0 (next to the
-// face) and its neighbour c1 (Sec. 4(2)): g1 next to the face, g2 outside it.
-__device__ __forceinline__ void x_face_layers(const Model<float>& m, int kind, const float c0[NV], const float c1[NV],
-                                              float g1[NV], float g2[NV]) {
-  float M0[5], M1[5], G1[5], G2[5];
-  moments(m, c0, M0[0], M0[1], M0[2], M0[3], M0[4]);
-  if (kind == LBM_BC_EXTRAPOLATE) {
-    moments(m, c1, M1[0], M1[1], M1[2], M1[3], M1[4]);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      G1[q] = 2.f * M0[q] - M1[q];
-      G2[q] = 2.f * G1[q] - M0[q];
-    }
-  } else {  // LBM_BC_REFLECT, normal velocity u1
-#pragma unroll
-    for (int q = 0; q < 5; ++q) G1[q] = G2[q] = M0[q];
-    G1[1] = 0.f;
-    G2[1] = -M0[1];
-  }
-  equilibrium(m, G1[0], G1[1], G1[2], G1[3], G1[4], g1);
-  equilibrium(m, G2[0], G2[1], G2[2], G2[3], G2[4], g2);
 }
 
 // One z-march unit: the TX x TY column at (x0, y0), planes z0 .. z0+nzc-1.
@@ -234,15 +173,9 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     const float* P0 = slot(0);
     const float* P1 = slot(1);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const int sz = vsign(i, 2);
-      const float2 fc = ld2(P0 + i * PL + c);
-      if (sz > 0) carry[i] = mmc2(sub(h1[i], h2[i]), sub(fc, h1[i]));
-      if (sz < 0) carry[i] = mmc2(sub(ld2(P1 + i * PL + c), fc), sub(fc, h1[i]));
-    }
+    for (int i = 0; i < NV; ++i) carry[i] = pm::carry0(i, h2[i], h1[i], ld2(P0 + i * PL + c), ld2(P1 + i * PL + c));
   }
 
-  const float2 half = bc2(0.5f);
   // F: the own pair of cell plane k; Fn: that of plane k+1, read as the z
   // neighbour during plane k and kept in registers for the next plane
   float2 F[NV], Fn[NV];
@@ -257,209 +190,16 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     const float* P2 = slot(k + 2);
 
 
-    // moments (relations e1-e3)
-    const float2 sa = add(add(add(F[1], F[2]), add(F[3], F[4])), add(F[5], F[6]));
-    const float2 dpp = add(F[7], F[8]), dpm = add(F[9], F[10]), dmp = add(F[11], F[12]), dmm = add(F[13], F[14]);
-    const float2 sd = add(add(dpp, dpm), add(dmp, dmm));
-    float2 rho = add(add(F[0], sa), sd);
-    const float2 mx = fma2(bc2(m.c1), sub(F[1], F[2]), mul(bc2(m.s), sub(add(dpp, dpm), add(dmp, dmm))));
-    const float2 my = fma2(bc2(m.c1), sub(F[3], F[4]), mul(bc2(m.s), sub(add(dpp, dmp), add(dpm, dmm))));
-    const float2 mz = fma2(bc2(m.c1), sub(F[5], F[6]),
-                           mul(bc2(m.s), sub(add(add(F[7], F[9]), add(F[11], F[13])),
-                                             add(add(F[8], F[10]), add(F[12], F[14])))));
-    const float2 E = fma2(bc2(m.eta0sq), F[0], fma2(bc2(m.c1sq), sa, mul(bc2(m.c2sq), sd)));
-    const float2 ir = make_float2(__frcp_rn(rho.x), __frcp_rn(rho.y));
-    float2 ux = mul(mx, ir), uy = mul(my, ir), uz = mul(mz, ir);
-    float2 usq = fma2(ux, ux, fma2(uy, uy, mul(uz, uz)));
-    float2 T = mul(sub(mul(E, ir), usq), bc2(m.inv_b));
-    if (rd.on) {
-      // ill-conditioned FP32 temperature (RecoverDesc): redo the cell in FP64
-      const float2 Aa = fma2(bc2(m.AaT), T, fma2(bc2(m.AaU), usq, bc2(m.Aa0)));
-      const float2 Ad = fma2(bc2(m.AdT), T, fma2(bc2(m.AdU), usq, bc2(m.Ad0)));
-      const float lhs0 = fmaf(rd.axis_w, fabsf(Aa.x), fmaf(rd.diag_w, fabsf(Ad.x), usq.x));
-      const float lhs1 = fmaf(rd.axis_w, fabsf(Aa.y), fmaf(rd.diag_w, fabsf(Ad.y), usq.y));
-      const bool need0 = act0 && !(lhs0 <= rd.thresh_b * T.x);
-      const bool need1 = act1 && !(lhs1 <= rd.thresh_b * T.y);
-      if (need0 || need1) {
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          if (!(h == 0 ? need0 : need1)) continue;
-          const Macro1 r = recover_fp64(P0 + c + h, PL, rd.c1, rd.s, rd.eta0sq, rd.c1sq, rd.c2sq, rd.inv_b);
-          if (h == 0) {
-            rho.x = r.rho; ux.x = r.ux; uy.x = r.uy; uz.x = r.uz; T.x = r.T;
-          } else {
-            rho.y = r.rho; ux.y = r.ux; uy.y = r.uy; uz.y = r.uz; T.y = r.T;
-          }
-        }
-        usq = fma2(ux, ux, fma2(uy, uy, mul(uz, uz)));
-      }
-    }
-    {
-      const float ax[2] = {rho.x, rho.y}, tt[2] = {T.x, T.y};
-      const float chk[2] = {fabsf(rho.x) + fabsf(T.x) + fabsf(ux.x) + fabsf(uy.x) + fabsf(uz.x),
-                            fabsf(rho.y) + fabsf(T.y) + fabsf(ux.y) + fabsf(uy.y) + fabsf(uz.y)};
-      const bool on[2] = {act0, act1};
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!on[h]) continue;
-        if (!(ax[h] > 0.f)) bad |= LBM_HEALTH_RHO;
-        if (!(tt[h] > 0.f)) bad |= LBM_HEALTH_T;
-        if (!(chk[h] < 1e30f)) bad |= LBM_HEALTH_NONFINITE;
-      }
-    }
-    // equilibrium (Eq. "eq"), per shell A + B w + D w^2
-    float2 feq[NV];
-    feq[0] = mul(rho, mul(bc2(m.AR), T));
-    {
-      const float2 Aa = fma2(bc2(m.AaT), T, fma2(bc2(m.AaU), usq, bc2(m.Aa0)));
-      const float2 Ba = fma2(bc2(m.BaT), T, fma2(bc2(m.BaU), usq, bc2(m.Ba0)));
-      const float2 u3[3] = {ux, uy, uz};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float2 w = mul(bc2(m.c1), u3[a]);
-        const float2 q = fma2(bc2(m.Da), mul(w, w), Aa);
-        const float2 l = mul(Ba, w);
-        feq[1 + 2 * a] = mul(rho, add(q, l));
-        feq[2 + 2 * a] = mul(rho, sub(q, l));
-      }
-      const float2 Ad = fma2(bc2(m.AdT), T, fma2(bc2(m.AdU), usq, bc2(m.Ad0)));
-      const float2 Bd = fma2(bc2(m.BdT), T, fma2(bc2(m.BdU), usq, bc2(m.Bd0)));
-      const float2 sxy = add(ux, uy), dxy = sub(ux, uy);
-      const float2 w4[4] = {mul(bc2(m.s), add(sxy, uz)), mul(bc2(m.s), sub(sxy, uz)), mul(bc2(m.s), add(dxy, uz)),
-                            mul(bc2(m.s), sub(dxy, uz))};
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const float2 q = fma2(bc2(m.Dd), mul(w4[kk], w4[kk]), Ad);
-        const float2 l = mul(Bd, w4[kk]);
-        feq[7 + kk] = mul(rho, add(q, l));
-        feq[14 - kk] = mul(rho, sub(q, l));
-      }
-    }
-
+    // moments (relations e1-e3), health, equilibrium and the per-field update
+    const pm::Mom r = pm::moments(m, rd, F, P0, c, PL, act0, act1);
+    bad |= pm::health(r, act0, act1);
     float2 out[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      const float* q = P0 + i * PL + c;
-      const float2 B = F[i];
-      float2 conv = make_float2(0.f, 0.f);
-      float2 S = make_float2(0.f, 0.f);
-      // ---- x: neighbour pairs A = (x-2, x-1), C = (x+2, x+3)
-      {
-        const int sg = vsign(i, 0);
-        if (sg != 0 || i <= 6) {
-          const float2 A = ld2(q - 2), C = ld2(q + 2);
-          const float e1 = B.x - A.y, e2 = B.y - B.x, e3 = C.x - B.y;
-          if (sg > 0) {
-            const float e0 = A.y - A.x;
-            float2 G;
-            if (SCHEME == LBM_SCHEME_NND) {
-              const float lo1 = fminf(e1, 0.f), hi1 = fmaxf(e1, 0.f);
-              const float m12 = mmc(e2, lo1, hi1), m01 = mmc(e0, lo1, hi1);
-              const float m23 = mmc(e3, fminf(e2, 0.f), fmaxf(e2, 0.f));
-              G = fma2(half, sub(make_float2(m12, m23), make_float2(m01, m12)), make_float2(e1, e2));
-            } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-              // (3 c - 4 m1 + m2) / 2: cell x (A.x, A.y, B.x), cell x+1 (A.y, B.x, B.y)
-              G = mul(half, add(fma2(bc2(3.f), B, mul(bc2(-4.f), make_float2(A.y, B.x))), A));
-            } else {
-              G = make_float2(e1, e2);
-            }
-            conv = add(conv, G);
-          } else if (sg < 0) {
-            const float e4 = C.y - C.x;
-            float2 G;
-            if (SCHEME == LBM_SCHEME_NND) {
-              const float lo2 = fminf(e2, 0.f), hi2 = fmaxf(e2, 0.f);
-              const float m23 = mmc(e3, lo2, hi2), m12 = mmc(e1, lo2, hi2);
-              const float m34 = mmc(e4, fminf(e3, 0.f), fmaxf(e3, 0.f));
-              G = fma2(bc2(-0.5f), sub(make_float2(m23, m34), make_float2(m12, m23)), make_float2(e2, e3));
-            } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-              // (4 p1 - 3 c - p2) / 2: cell x (B.x, B.y, C.x), cell x+1 (B.y, C.x, C.y)
-              const float2 P1x = make_float2(B.y, C.x);
-              G = mul(half, sub(fma2(bc2(4.f), P1x, mul(bc2(-3.f), B)), C));
-            } else {
-              G = make_float2(e2, e3);
-            }
-            conv = sub(conv, G);
-          }
-          if (i <= 6) S = add(S, make_float2(A.y + B.y, B.x + C.x));
-        }
-      }
-      // ---- y: rows y-2 .. y+2 of the same pair
-      {
-        const int sg = vsign(i, 1);
-        if (sg != 0 || i <= 6) {
-          const float2 M1 = ld2(q - BX), P1y = ld2(q + BX);
-          if (sg > 0) {
-            const float2 M2 = ld2(q - 2 * BX);
-            const float2 D0 = sub(B, M1);
-            float2 G;
-            if (SCHEME == LBM_SCHEME_NND) {
-              G = fma2(half, sub(mmc2(sub(P1y, B), D0), mmc2(sub(M1, M2), D0)), D0);
-            } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-              G = mul(half, add(fma2(bc2(3.f), B, mul(bc2(-4.f), M1)), M2));
-            } else {
-              G = D0;
-            }
-            conv = add(conv, G);
-          } else if (sg < 0) {
-            const float2 P2y = ld2(q + 2 * BX);
-            const float2 D1 = sub(P1y, B);
-            float2 G;
-            if (SCHEME == LBM_SCHEME_NND) {
-              G = fma2(bc2(-0.5f), sub(mmc2(sub(P2y, P1y), D1), mmc2(sub(B, M1), D1)), D1);
-            } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-              G = mul(half, sub(fma2(bc2(4.f), P1y, mul(bc2(-3.f), B)), P2y));
-            } else {
-              G = D1;
-            }
-            conv = sub(conv, G);
-          }
-          if (i <= 6) S = add(S, add(M1, P1y));
-        }
-      }
-      // ---- z: planes z+1, z+2 from the ring, z-1 (z-2) from registers
-      {
-        const int sg = vsign(i, 2);
-        const float2 Z1 = ld2(P1 + i * PL + c);
-        Fn[i] = Z1;
-        const float2 H = h1[i];
-        if (sg > 0) {
-          const float2 D0 = sub(B, H);
-          float2 G;
-          if (SCHEME == LBM_SCHEME_NND) {
-            const float2 mA = mmc2(sub(Z1, B), D0);
-            G = fma2(half, sub(mA, carry[i]), D0);
-            carry[i] = mA;
-          } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-            G = mul(half, add(fma2(bc2(3.f), B, mul(bc2(-4.f), H)), h2[i]));
-          } else {
-            G = D0;
-          }
-          conv = add(conv, G);
-        } else if (sg < 0) {
-          const float2 Z2 = ld2(P2 + i * PL + c);
-          const float2 D1 = sub(Z1, B);
-          float2 G;
-          if (SCHEME == LBM_SCHEME_NND) {
-            const float2 mA = mmc2(sub(Z2, Z1), D1);
-            G = fma2(bc2(-0.5f), sub(mA, carry[i]), D1);
-            carry[i] = mA;
-          } else if (SCHEME == LBM_SCHEME_UPWIND2) {
-            G = mul(half, sub(fma2(bc2(4.f), Z1, mul(bc2(-3.f), B)), Z2));
-          } else {
-            G = D1;
-          }
-          conv = sub(conv, G);
-        }
-        if (i <= 6) S = add(S, add(H, Z1));
-      }
-      const float keep = i == 0 ? m.keep0 : (i <= 6 ? m.keep1 : m.keep2);
-      const float kk = i == 0 ? 0.f : (i <= 6 ? m.k1 : m.k2);
-      const float lam = i == 0 ? m.lam0 : (i <= 6 ? m.lam1 : 0.f);
-      float2 o = fma2(bc2(m.dt_tau), feq[i], mul(bc2(keep), B));
-      if (i != 0) o = fma2(bc2(-kk), conv, o);
-      if (i <= 6) o = fma2(bc2(lam), S, o);
-      out[i] = o;
+      const float2 Z1 = ld2(P1 + i * PL + c);
+      Fn[i] = Z1;
+      out[i] = pm::field_update<SCHEME, BX>(m, i, P0 + i * PL + c, F[i], Z1, P2 + i * PL + c, h1[i], h2[i],
+                                            carry[i], pm::feq(m, r, i));
     }
     const long long g = gbase + (long long)k * L.plane;
     if (act1) {
@@ -502,7 +242,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
             c0[i] = side == 0 ? out[i].x : out[i].y;  // the cell next to the face
             c1[i] = side == 0 ? out[i].y : out[i].x;
           }
-          x_face_layers(m, side == 0 ? wt.xlo : wt.xhi, c0, c1, g1, g2);
+          pm::x_face_layers(m, side == 0 ? wt.xlo : wt.xhi, c0, c1, g1, g2);
           const long long at = side == 0 ? L.at(-2, y, z) : L.at(L.nx, y, z);
 #pragma unroll
           for (int i = 0; i < NV; ++i)

@@ -289,11 +289,14 @@ bool make_tmap(CUtensorMap* map, void* base, const Layout& L, int bx, int by) {
 }
 
 // Variants whose step kernel writes the boundary layers of its output.
-bool wt_variant(int variant) { return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED64; }
+bool wt_variant(int variant) {
+  return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED64 || variant == LBM_VARIANT_TILED_SPLIT;
+}
 
 // Variants that run the pair kernel, and its tile width.
 bool pair_variant(int variant) {
-  return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED_FILL || variant == LBM_VARIANT_TILED64;
+  return variant == LBM_VARIANT_TILED || variant == LBM_VARIANT_TILED_FILL || variant == LBM_VARIANT_TILED64 ||
+         variant == LBM_VARIANT_TILED_SPLIT;
 }
 int pair_cols(int variant) { return variant == LBM_VARIANT_TILED64 ? 64 : 32; }
 
@@ -463,7 +466,8 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
         !make_tmap(&s->tmap[1], s->fbuf[1], s->L, lbm::tiled_box_x(), lbm::tiled_box_y()) ||
         !make_tmap(&s->wmap[0], s->fbuf[0], s->L, p64.bx, p64.by) ||
         !make_tmap(&s->wmap[1], s->fbuf[1], s->L, p64.bx, p64.by) ||
-        lbm::prepare_tiled_kernels() != cudaSuccess || lbm::prepare_pair_kernels() != cudaSuccess) {
+        lbm::prepare_tiled_kernels() != cudaSuccess || lbm::prepare_pair_kernels() != cudaSuccess ||
+        lbm::prepare_split_kernels() != cudaSuccess) {
       delete s;
       return LBM_ECUDA;
     }
@@ -495,7 +499,7 @@ int lbm_set_scheme(lbm_sim* s, int32_t scheme, int32_t dissipation) {
 int lbm_set_launch(lbm_sim* s, int32_t variant, int32_t zchunk, int32_t ztail) {
   if (!s) return LBM_EINVAL;
   if (s->failed) return LBM_ESTATE;
-  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED64 || zchunk < 0 || ztail < 0) return LBM_EINVAL;
+  if (variant < LBM_VARIANT_TILED || variant > LBM_VARIANT_TILED_SPLIT || zchunk < 0 || ztail < 0) return LBM_EINVAL;
   s->variant = variant;
   s->zchunk = zchunk;
   s->ztail = ztail;
@@ -570,9 +574,14 @@ int run_steps(lbm_sim* s, int64_t n) {
       if (pair) {
         const CUtensorMap& map = shape.tx == 64 ? s->wmap[s->cur] : s->tmap[s->cur];
         const lbm::ZSched zs = lbm::make_zsched(s->L.nz, zc, s->zchunk > 0 ? s->ztail : auto_ztail(zc));
-        LBM_LAUNCH(s, LBM_KERNEL_STEP,
-                   lbm::launch_step_pair(shape.tx, s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf, wt,
-                                         s->rd, zs, s->flags, s->wait_limit, s->st));
+        if (s->variant == LBM_VARIANT_TILED_SPLIT)
+          LBM_LAUNCH(s, LBM_KERNEL_STEP,
+                     lbm::launch_step_split(s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf, wt, s->rd, zs,
+                                            s->flags, s->wait_limit, s->st));
+        else
+          LBM_LAUNCH(s, LBM_KERNEL_STEP,
+                     lbm::launch_step_pair(shape.tx, s->scheme, map, (const float*)fin, (float*)fout, s->L, s->mf,
+                                           wt, s->rd, zs, s->flags, s->wait_limit, s->st));
       } else {
         LBM_LAUNCH(s, LBM_KERNEL_STEP,
                    lbm::launch_step_tiled(s->scheme, s->tmap[s->cur], (const float*)fin, (float*)fout, s->L, s->mf,
@@ -653,7 +662,10 @@ int run_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
     tab.done = s0->done;
     const long long resident = (long long)shape.ctas_per_sm * s0->num_sms;
     const int grid = (int)(units < resident ? units : resident);
-    LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(shape.tx, s0->scheme, tab, grid, s0->st));
+    if (s0->variant == LBM_VARIANT_TILED_SPLIT)
+      LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_split_batch(s0->scheme, tab, grid, s0->st));
+    else
+      LBM_LAUNCH(s0, LBM_KERNEL_STEP, lbm::launch_step_pair_batch(shape.tx, s0->scheme, tab, grid, s0->st));
     for (int i = 0; i < n; ++i) {
       lbm_sim* s = sims[i];
       s->layers_ok[s->cur ^ 1] = 1;

@@ -280,10 +280,18 @@ struct BatchTable {
 };
 // Batched step over the descriptor table (`cols` x 8 tiles, maps of that box).
 cudaError_t launch_step_pair_batch(int cols, int scheme, const BatchTable& tab, int grid, cudaStream_t st);
+// Field-split kernel on 32 x 8 tiles (two warp groups of 128 threads per
+// tile, two CTAs per SM; the 40 x 12 map of the pair kernel), single grid and
+// batched; results bitwise equal to the pair kernel's.
+cudaError_t launch_step_split(int scheme, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
+                              const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
+                              unsigned* flags, unsigned wait_limit, cudaStream_t st);
+cudaError_t launch_step_split_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st);
 // Shared-memory attributes of the tiled kernels; set once per device before
 // their first launch (not allowed inside a stream capture).
 cudaError_t prepare_tiled_kernels();
 cudaError_t prepare_pair_kernels();
+cudaError_t prepare_split_kernels();
 // Geometry of the tiled kernel's TMA box (x, y extents) and CTA tile.
 int tiled_box_x();
 int tiled_box_y();

@@ -105,13 +105,14 @@ class Sim:
 
     def set_launch(self, variant="tiled", zchunk: int = 0, ztail: int = 0):
         """FP32 step kernel: "tiled" (32 x 8 TMA plane tiles, cell pairs, boundary layers
-        written by the step; default), "tiled64" (the same on 64 x 8 tiles), "tiled_fill"
+        written by the step; default), "tiled64" (the same on 64 x 8 tiles), "split" (the
+        32 x 8 tiles with two warp groups, each updating part of the 15 fields), "tiled_fill"
         (boundary layers by a fill launch), "tiled_single" (one cell per thread) or "plain";
         zchunk = z planes per CTA (0 = auto); ztail > 0 (pair kernels): the end of each
         tile column is split into short chunks of ztail planes, launched last."""
         v = {"tiled": A.LBM_VARIANT_TILED, "plain": A.LBM_VARIANT_PLAIN,
              "tiled_single": A.LBM_VARIANT_TILED_SINGLE, "tiled_fill": A.LBM_VARIANT_TILED_FILL,
-             "tiled64": A.LBM_VARIANT_TILED64}[variant] \
+             "tiled64": A.LBM_VARIANT_TILED64, "split": A.LBM_VARIANT_TILED_SPLIT}[variant] \
             if isinstance(variant, str) else int(variant)
         A.check(A.lbm_set_launch(self._h, v, int(zchunk), int(ztail)), "lbm_set_launch")
         self.launch = (variant, int(zchunk), int(ztail))

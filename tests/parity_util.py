@@ -77,3 +77,48 @@ def l1_rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+# ---------------------------------------------------------------- FP32 error model
+#
+# The FP32 path stores and updates f in float.  Per time step every stored
+# value picks up C_ROUND roundings of relative size U32 = 2^-24, counted along
+# the kernel's path of one value: the moment sums (five levels of the
+# summation tree), three more for the temperature, five in the equilibrium
+# (Eq. "eq" as A + B w + D w^2 and the product with rho) and three fused
+# multiply-adds in the update, the last of which is the stored rounding.
+# Taken coherent within a step, they put an error of C_ROUND U32 kappa rho
+# into a cell's density, where the condition number kappa of a state is the
+# larger of
+#   kappa_rho = sum_i |f_i^eq| / rho                         (relation e1)
+#   kappa_T   = sum_i |f_i^eq| (|v_i|^2 + eta_i^2) / (rho b T)  (e3 for T)
+# (the equilibrium's populations are of both signs, so the sums cancel).
+# Across steps the errors are independent and the scheme damps them (a single
+# perturbation of the initial state shrinks), so they add as a random walk:
+#   L1(n) <= C_ROUND U32 kappa_max sqrt(n),
+# kappa_max over the states of the workload.  The bound is fixed by the
+# model, not by measurement.
+U32 = 2.0 ** -24
+C_ROUND = 16
+
+
+def kappa(cfg, state):
+    """Condition number (max of kappa_rho, kappa_T) of the macroscopic state
+    (rho, u1, u2, u3, T) under the model constants of cfg."""
+    v, eta = oracle.velocities(cfg)
+    fe = oracle.feq(cfg, state[0], state[1:4], state[4])
+    b = 2.0 / (cfg.gamma - 1.0)
+    k_rho = np.abs(fe).sum() / state[0]
+    k_T = (np.abs(fe) * ((v * v).sum(1) + eta * eta)).sum() / (state[0] * b * state[4])
+    return float(max(k_rho, k_T))
+
+
+def fp32_l1_bound(cfg, states, nsteps):
+    """The FP32 model's bound on the L1 relative density error after nsteps."""
+    return C_ROUND * U32 * max(kappa(cfg, s) for s in states) * float(np.sqrt(max(1, nsteps)))
+
+
+def linf_rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / np.abs(b).max())

@@ -33,7 +33,8 @@ def _mix_sims(seed):
 
 
 @pytest.mark.parametrize("variant,zchunk,ztail", [("tiled", 0, 0), ("tiled", 5, 2), ("tiled", 3, 1),
-                                                  ("tiled64", 0, 0), ("tiled64", 4, 3)])
+                                                  ("tiled64", 0, 0), ("tiled64", 4, 3), ("split", 0, 0),
+                                                  ("split", 5, 2)])
 def test_batch_results_equal_alone(variant, zchunk, ztail):
     """Batched (any tile shape and chunking) equals each grid stepped alone
     with the default launch: bitwise."""

@@ -26,7 +26,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("variant", ["tiled", "tiled64"])
+@pytest.mark.parametrize("variant", ["tiled", "tiled64", "split"])
 def test_wait_that_runs_out_reports_timeout_and_device_stays_usable(variant):
     from paper_1010_4135_gb300 import _abi as A
     cfg = case_cfg("periodic_37x19x11")

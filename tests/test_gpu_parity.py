@@ -46,7 +46,7 @@ def test_fp64_step_parity(name, scheme):
     assert s.steps_done == STEPS
 
 
-@pytest.mark.parametrize("variant", ["tiled", "tiled64", "tiled_fill", "tiled_single", "plain"])
+@pytest.mark.parametrize("variant", ["tiled", "tiled64", "split", "tiled_fill", "tiled_single", "plain"])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_step_parity(name, variant):
     cfg = case_cfg(name)
@@ -62,7 +62,7 @@ def test_fp32_step_parity(name, variant):
     assert err.max() <= FP32_TOL, err
 
 
-@pytest.mark.parametrize("variant", ["tiled", "tiled64", "tiled_single"])
+@pytest.mark.parametrize("variant", ["tiled", "tiled64", "split", "tiled_single"])
 @pytest.mark.parametrize("scheme", [oracle.UPWIND2, oracle.UPWIND1])
 def test_fp32_tiled_other_schemes(scheme, variant):
     cfg = case_cfg("fixed_extrap_reflect_33x17x9", scheme=scheme)
@@ -75,7 +75,7 @@ def test_fp32_tiled_other_schemes(scheme, variant):
     assert field_errors(s.get_f(), ref).max() <= FP32_TOL
 
 
-@pytest.mark.parametrize("variant", ["tiled", "tiled64", "tiled_single"])
+@pytest.mark.parametrize("variant", ["tiled", "tiled64", "split", "tiled_single"])
 def test_fp32_tiled_results_do_not_depend_on_z_chunking(variant):
     cfg = case_cfg("periodic_37x19x11")
     f0 = initial_f(cfg, seed=12).astype(np.float32)
@@ -97,7 +97,7 @@ def test_fp32_variants_agree():
     cfg = case_cfg("wide_70x9x5")
     f0 = initial_f(cfg, seed=13).astype(np.float32)
     res = {}
-    for v in ("tiled", "tiled64", "tiled_fill", "tiled_single", "plain"):
+    for v in ("tiled", "tiled64", "split", "tiled_fill", "tiled_single", "plain"):
         s = sim_for(cfg, "fp32")
         s.set_launch(v)
         s.set_f(f0)
@@ -107,6 +107,8 @@ def test_fp32_variants_agree():
     assert np.array_equal(res["tiled"], res["tiled_fill"])
     # the two tile shapes of the pair kernel run the same per-cell arithmetic
     assert np.array_equal(res["tiled"], res["tiled64"])
+    # and so does the field-split kernel (two warp groups per tile)
+    assert np.array_equal(res["tiled"], res["split"])
     # same formulas, different association of float operations: ulp-level
     # differences (2^-24 ~ 6e-8) over ten steps of ~100 operations each
     assert field_errors(res["tiled"], res["plain"]).max() <= 1e-5

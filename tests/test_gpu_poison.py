@@ -30,7 +30,7 @@ def _sim(cfg, precision, fill):
                  fixed_hi=cfg.fixed_hi, scheme=scheme, workspace=ws)
 
 
-@pytest.mark.parametrize("precision,variant", [("fp32", "tiled"), ("fp32", "tiled64"), ("fp32", "tiled_fill"),
+@pytest.mark.parametrize("precision,variant", [("fp32", "tiled"), ("fp32", "tiled64"), ("fp32", "split"), ("fp32", "tiled_fill"),
                                                ("fp32", "tiled_single"), ("fp32", "plain"), ("fp64", "plain")])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_unread_layers_poisoned_with_nan_do_not_matter(name, precision, variant):

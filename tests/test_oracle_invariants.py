@@ -112,3 +112,31 @@ def test_step_nodes_matches_full_step():
     out = oracle.step_nodes(cfg, f, xyz)
     for k, (x, y, z) in enumerate(xyz):
         assert np.array_equal(out[k], g[:, z, y, x])
+
+
+@pytest.mark.parametrize("gamma", [1.4, 5.0 / 3.0])
+def test_conserved_closed_form_of_uniform_equilibria(gamma):
+    """oracle.conserved against the closed form of relations e1-e3 (Sec. 2):
+    a cell holding f^eq(rho, u, T) carries mass rho, momentum rho u and
+    energy rho (b T + |u|^2) with b = 2 / (gamma - 1).  Two states with
+    momentum components of different sizes and signs fill the two halves of
+    the grid, so a swapped, dropped or sign-flipped velocity weight, a
+    missing eta_0 term or a wrong energy weight changes a sum."""
+    cfg = oracle.Cfg(nx=6, ny=4, nz=3, gamma=gamma, c1=2.0, c2=6.0, eta0=3.0)
+    b = 2.0 / (gamma - 1.0)
+    A = (1.3, 0.4, -0.7, 0.25, 0.9)
+    B = (0.6, -1.1, 0.3, 0.8, 2.5)
+    left = np.zeros((cfg.nz, cfg.ny, cfg.nx), dtype=bool)
+    left[..., : cfg.nx // 2] = True
+    rho = np.where(left, A[0], B[0])
+    u = np.stack([np.where(left, A[1 + a], B[1 + a]) for a in range(3)])
+    T = np.where(left, A[4], B[4])
+    got = oracle.conserved(cfg, oracle.init(cfg, rho, u, T))
+    half = cfg.ncell // 2
+
+    def cell(s):
+        usq = s[1] ** 2 + s[2] ** 2 + s[3] ** 2
+        return np.array([s[0], s[0] * s[1], s[0] * s[2], s[0] * s[3], s[0] * (b * s[4] + usq)])
+
+    want = half * (cell(A) + cell(B))
+    assert np.all(np.abs(got - want) <= 1e-12 * np.abs(want)), (got, want)
