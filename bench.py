@@ -56,6 +56,8 @@ def parse():
                    help="with --zchunk: short chunks of this many planes end each tile column (0 = none)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the FP64 reference run behind the line's accuracy object")
     return p.parse_args()
 
 
@@ -130,6 +132,12 @@ def run_batch(args):
     clock = clocks.summary(t0, t1)
     clocks.stop()
     health = [s.health() for s in sims]
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = []
+        for w, s in zip(ws, sims):
+            r32, _, _ = s.moments()
+            accuracy.append(fp32_accuracy(w, r32, s.steps_done))
     peak, peak_kind = measured_peak()
     alg = 120.0 * cells
     per_step = ms * 1e-3 / steps
@@ -148,10 +156,30 @@ def run_batch(args):
                      "frac": alg / per_step / 1e9 / peak, "peak_source": peak_kind,
                      "kernel": "step_pair_batch (all grids, one launch per step; time per step incl. graph gaps)",
                      "traffic": None},
+        "accuracy": accuracy,
         "gpu_launches": steps, "clocks": clock, "health_flags": health,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fp32_accuracy(w, r32, steps):
+    """L1 / Linf relative density error of an FP32 result after `steps`
+    steps against the FP64 path run alone from the same initial fields (the
+    FP64 path equals the oracle to 1e-12 on the parity cases and on one
+    full-size step of the benchmarked grids)."""
+    import numpy as np
+    from paper_1010_4135_gb300 import sim as S
+    s64 = S.from_workload(w, precision="fp64")
+    rho, u, T = w.initial_fields()
+    s64.init(rho, u, T)
+    s64.step(steps)
+    r64, _, _ = s64.moments()
+    s64.close()
+    r32 = np.asarray(r32, dtype=np.float64).reshape(r64.shape)
+    return {"grid": w.name, "steps": int(steps), "vs": "fp64 path",
+            "l1_rho": float(np.abs(r32 - r64).sum() / np.abs(r64).sum()),
+            "linf_rho": float(np.abs(r32 - r64).max() / np.abs(r64).max())}
 
 
 def describe(w, precision):
@@ -424,6 +452,18 @@ def run_ours(args):
                "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
                "note": "per run: lbm_init from pinned host (rho,u,T) + steps + lbm_moments to pinned host"}
 
+    # FP32 density error of a run of args.steps steps against the FP64 path
+    accuracy = None
+    if not args.no_accuracy and args.precision == "fp32" and rank == 0:
+        if e2e is not None:
+            r32 = orho.numpy()  # the end-to-end run: init, args.steps steps, moments
+        else:
+            s.init(rho, u, T)
+            s.step(args.steps)
+            r32, _, _ = s.moments()
+        accuracy = fp32_accuracy(w, r32, args.steps)
+        accuracy["metric"] = "L1 = sum|rho32 - rho64| / sum|rho64|; Linf = max|rho32 - rho64| / max|rho64|"
+
     if rank != 0:
         replicas.finish()
         return 0
@@ -462,6 +502,7 @@ def run_ours(args):
                               "autotuned": tuned is not None,
                               "tune_timings_ms": tuned.get("timings") if tuned else None}},
         "roofline": roofline,
+        "accuracy": accuracy,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(step_n + fill_n) * world,

