@@ -16,8 +16,14 @@
 // Calls whose kernels overlap on the same GPU (for example, calls issued on
 // two streams without ordering between them) race on the array and give wrong
 // sums.  The first call on each device looks up the array's device address
-// (cudaGetSymbolAddress with that device current); make that first call
-// before any stream capture begins.
+// (cudaGetSymbolAddress with that device current) and loads both kernel
+// instantiations; make that first call before any stream capture begins.
+// The address is kept together with the unique id of the CUDA context it came
+// from: after cudaDeviceReset (or any teardown of the device's context) the
+// next call finds a new context id and looks the address up again, so no
+// call uses an address of a destroyed context.  With the output in host
+// memory the call synchronises its stream, which a stream under capture
+// cannot do: such calls are refused (LBM_EINVAL) before anything is queued.
 #include <cmath>
 #include <mutex>
 
@@ -104,20 +110,57 @@ __global__ void __launch_bounds__(kNoallocThreads)
 
 std::mutex g_setup_mutex;
 NoallocScratch* g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};  // id of the context the address belongs to
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry point (no -lcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* p = nullptr;
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r1, r2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1) != cudaSuccess ||
+        r1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2) != cudaSuccess ||
+        r2 != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    get_current = (CtxGetCurrentFn)p;
+    get_id = (CtxGetIdFn)q;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch array on the current device.  Looked up
+// (cudaGetSymbolAddress with that device current) on the first call and
+// again whenever the device's context has changed since; the set-up also
+// loads both kernel instantiations, so a later call enqueues launches only.
+// The caller has made a runtime call on this device already, so its primary
+// context is current.
 cudaError_t scratch_for_current_device(NoallocScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned long long ctx = 0;
+  e = current_context_id(&ctx);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, noalloc_conserved_kernel<float>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, noalloc_conserved_kernel<double>);
+    if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = (NoallocScratch*)p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -135,9 +178,13 @@ extern "C" int lbm_conserved_noalloc(const void* f, int32_t precision, int32_t n
   const long long n = (long long)nx * ny * nz;
   if (n > kNoallocMaxCells) return LBM_EINVAL;  // the static scratch holds 4096 block partials
   if (!(vset->c1 > 0) || !(vset->c2 > 0) || !(vset->eta0 > 0)) return LBM_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // also makes the device's primary context current for the lookup below
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return LBM_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone && !out_on_device) return LBM_EINVAL;  // cannot synchronise
   NoallocScratch* scr = nullptr;
   if (scratch_for_current_device(&scr) != cudaSuccess) return LBM_ECUDA;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   Consts m;
   m.c1 = vset->c1;
   m.s = vset->c2 / std::sqrt(3.0);

@@ -18,7 +18,9 @@ host).  Waiting requests are admitted in arrival order (policy "fifo", the
 default: a request that does not fit the memory left blocks the ones behind
 it), or shortest job first (policy "sjf": among the prepared requests that fit,
 the one with the fewest cell-updates; re-solves first), which cuts the
-median latency under overload at the cost of the largest requests.
+median latency under overload at the cost of the largest requests.  SJF
+bounds the wait: a request that later arrivals have overtaken MAX_BYPASS
+times is admitted next, before anything younger, as soon as it fits.
 
 A request whose result comes back unhealthy (health bits: rho <= 0, T <= 0,
 non-finite) is solved again with the next parameter candidate
@@ -56,6 +58,7 @@ class Job:
     admitted: float = 0.0
     finished: float = 0.0
     health: int = 0
+    bypassed: int = 0          # later arrivals admitted ahead of this job (SJF)
     rho: object = None
     # retirement in flight
     event: object = None
@@ -66,6 +69,7 @@ class Job:
 
 ATTEMPTS = 3  # parameter candidates per request
 POLICIES = ("fifo", "sjf")
+MAX_BYPASS = 32  # SJF: later arrivals that may overtake a waiting request
 
 
 def work(req) -> int:
@@ -74,15 +78,21 @@ def work(req) -> int:
     return int(nx) * int(ny) * int(nz) * int(req["steps"])
 
 
-def next_admission(waiting, used: int, budget: int, policy: str = "fifo"):
+def next_admission(waiting, used: int, budget: int, policy: str = "fifo", max_bypass: int = MAX_BYPASS):
     """The waiting job to admit next, or None: FIFO takes the head of the
     queue if it is prepared and fits the memory left; SJF takes, among the
     prepared jobs that fit, a re-solve first, else the one with the least
-    work (ties in arrival order)."""
+    work (ties in arrival order) -- unless a job has been overtaken
+    max_bypass times (`bypassed`, counted by note_admission): the oldest such
+    job goes next, and nothing else is admitted until it is prepared and
+    fits, so no request waits without bound while small ones keep arriving."""
     if policy == "fifo":
         if waiting and waiting[0].prep.done() and used + waiting[0].nbytes <= budget:
             return waiting[0]
         return None
+    starved = next((j for j in waiting if j.bypassed >= max_bypass), None)
+    if starved is not None:
+        return starved if starved.prep.done() and used + starved.nbytes <= budget else None
     best, key = None, None
     for j in waiting:
         if not j.prep.done() or used + j.nbytes > budget:
@@ -91,6 +101,15 @@ def next_admission(waiting, used: int, budget: int, policy: str = "fifo"):
         if key is None or k < key:
             best, key = j, k
     return best
+
+
+def note_admission(waiting, job):
+    """Count the overtaking: every job still waiting that arrived before
+    `job` (is ahead of it in the queue) has been bypassed once more."""
+    for j in waiting:
+        if j is job:
+            break
+        j.bypassed += 1
 
 
 def request_parameters(req, attempt: int = 0):
@@ -239,6 +258,7 @@ class Server:
                     j = next_admission(waiting, used, self.budget, self.policy)
                     if j is None:
                         break
+                    note_admission(waiting, j)
                     waiting.remove(j)
                     self._admit(j)
                     j.admitted = clock()

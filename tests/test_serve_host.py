@@ -21,6 +21,7 @@ class J:
     nbytes: int
     attempt: int = 0
     prep: object = dataclasses.field(default_factory=Done)
+    bypassed: int = 0
 
 
 def _job(i, grid, steps, nbytes, attempt=0, ready=True):
@@ -56,3 +57,33 @@ def test_work_and_policy_names():
 def test_unknown_policy_is_rejected_before_any_device_work():
     with pytest.raises(ValueError):
         serve.Server(hbm_budget=1, policy="lifo")
+
+
+def test_sjf_admits_a_big_job_within_a_bounded_number_of_admissions():
+    """Small jobs keep arriving (one per admission round, two batch slots'
+    worth of memory free): under SJF the big job that arrived first is
+    overtaken at most MAX_BYPASS times, then admitted before any younger
+    job; FIFO admits it first."""
+    for policy, limit in (("sjf", serve.MAX_BYPASS), ("fifo", 0)):
+        big = _job(0, (256, 256, 256), 3000, 60)
+        q = collections.deque([big])
+        admitted, rounds = [], 0
+        while big not in admitted:
+            rounds += 1
+            assert rounds <= 4 * serve.MAX_BYPASS + 4, policy
+            q.append(_job(rounds, (64, 64, 64), 500, 10))
+            j = serve.next_admission(q, used=0, budget=100, policy=policy)
+            assert j is not None
+            serve.note_admission(q, j)
+            q.remove(j)
+            admitted.append(j)
+        assert admitted.index(big) == limit, (policy, admitted.index(big))
+
+
+def test_a_starved_job_blocks_younger_ones_until_it_fits():
+    big = _job(0, (256, 256, 256), 3000, 60)
+    big.bypassed = serve.MAX_BYPASS
+    q = collections.deque([big, _job(1, (16, 16, 16), 10, 5)])
+    # the small job would fit, but the starved one goes first: nothing until memory frees up
+    assert serve.next_admission(q, used=50, budget=100, policy="sjf") is None
+    assert serve.next_admission(q, used=0, budget=100, policy="sjf") is big

@@ -5,9 +5,10 @@ CUDA graph, a host whose allocator owns the whole device, a monitoring hook
 that must not change the memory footprint).  For them the library offers one
 entry point whose scratch is a static device array instead of a workspace.
 This file checks it against the workspace-based lbm_conserved on the same
-state, through the C ABI, on two calls in a row (the second call reuses the
-shared array the first one left behind).  It is named so that pytest
-collects it last.
+state and against the oracle's sums of that state, through the C ABI, on two
+calls in a row (the second call reuses the shared array the first one left
+behind), and checks that a call leaves the device's free memory unchanged.
+It is named so that pytest collects it last.
 """
 import ctypes
 
@@ -47,15 +48,21 @@ def test_noalloc_matches_workspace_reduction(name, precision):
     s.get_f(dense)
     g = dense.cpu().numpy().astype(np.float64)
     scale = np.abs(oracle.conserved(cfg, np.abs(g)))
+    want = oracle.conserved(cfg, g)
     vset = A.make_vset(cfg.c1, cfg.c2, cfg.eta0, cfg.gamma)
     prec = A.LBM_FP32 if precision == "fp32" else A.LBM_FP64
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):  # two calls in a row: host output
+    for k in range(2):  # two calls in a row: host output
         out = np.zeros(5)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = A.lbm_conserved_noalloc(ctypes.c_void_p(dense.data_ptr()), prec, cfg.nx, cfg.ny, cfg.nz,
                                      ctypes.byref(vset), ctypes.c_void_p(out.ctypes.data), 0, stream)
         assert rc == A.LBM_OK
+        if k == 1:  # after the first call's set-up: the call allocates nothing on the device
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert np.all(np.abs(out - ref) <= CONSERVED_TOL * np.maximum(scale, 1e-300)), (out, ref)
+        assert np.all(np.abs(out - want) <= CONSERVED_TOL * np.maximum(scale, 1e-300)), (out, want)
     for _ in range(2):  # two calls in a row: device output
         out_d = torch.zeros(5, dtype=torch.float64, device="cuda")
         rc = A.lbm_conserved_noalloc(ctypes.c_void_p(dense.data_ptr()), prec, cfg.nx, cfg.ny, cfg.nz,
@@ -64,6 +71,7 @@ def test_noalloc_matches_workspace_reduction(name, precision):
         torch.cuda.synchronize()
         out = out_d.cpu().numpy()
         assert np.all(np.abs(out - ref) <= CONSERVED_TOL * np.maximum(scale, 1e-300)), (out, ref)
+        assert np.all(np.abs(out - want) <= CONSERVED_TOL * np.maximum(scale, 1e-300)), (out, want)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
