@@ -61,8 +61,11 @@ enum {
   LBM_BC_PERIODIC = 0,    /* wrap; both faces of the axis must be periodic */
   LBM_BC_FIXED = 1,       /* both layers hold the given (rho,u1,u2,u3,T) */
   LBM_BC_EXTRAPOLATE = 2, /* g1 = 2 m0 - m1, g2 = 2 g1 - m0 on rho, u, T (needs >= 2 cells) */
-  LBM_BC_REFLECT = 3      /* wall layer: (rho,T,u_t) of the last cell, u_n = 0;
+  LBM_BC_REFLECT = 3,     /* wall layer: (rho,T,u_t) of the last cell, u_n = 0;
                              outer layer: the last cell with u_n negated */
+  LBM_BC_EXTERNAL = 4     /* x faces only (needs >= 2 cells): the two layers hold the
+                             neighbouring slab's two columns, written by the caller
+                             (lbm_set_halo) before every step; see lbm_set_halo */
 };
 
 /* Storage and arithmetic precision of f. */
@@ -202,12 +205,39 @@ LBM_API int lbm_conserved(lbm_sim* sim, double out[5]);
  * live in one static 256 KiB device array that every GPU loading this library
  * keeps until exit.  At most 33,554,432 cells (4096 blocks of 8192 cells);
  * larger grids return LBM_EINVAL.  The first call on a device looks up the
- * array's address, so make it before any stream capture.  All calls share the
+ * array's address, so make it before any stream capture; the address is kept
+ * with the id of the device's CUDA context, and after a context reset
+ * (cudaDeviceReset) the next call looks it up again.  All calls share the
  * array: calls that overlap on the same GPU race and give wrong sums.  out is
  * 5 doubles, in device memory (out_on_device = 1; asynchronous on
- * cuda_stream) or host memory (the call synchronises cuda_stream). */
+ * cuda_stream) or host memory (the call synchronises cuda_stream; on a stream
+ * under capture, which cannot be synchronised, LBM_EINVAL before anything is
+ * queued). */
 LBM_API int lbm_conserved_noalloc(const void* f, int32_t precision, int32_t nx, int32_t ny, int32_t nz,
                                   const lbm_vset* vset, double* out, int32_t out_on_device, void* cuda_stream);
+
+/* Slab decomposition along x.  A grid cut into x-slabs (one sim per slab,
+ * on one or several GPUs) advances exactly as the whole grid when, before
+ * every step, each cut face's two outside layers hold the neighbouring
+ * slab's two boundary columns: the stencil of Sec. 3 reaches two cells along
+ * each axis and no further.  Faces at cuts are LBM_BC_EXTERNAL.
+ *   lbm_get_halo_source: the two interior columns next to x face `side`
+ *     (0 = lo: x = 0, 1; 1 = hi: x = nx-2, nx-1) of the current state, into
+ *     buf, dense [15][nz][ny][2] (x order) in the storage precision
+ *     (15 * ny * nz * 2 * 4 or 8 bytes).
+ *   lbm_set_halo: writes the two layers outside x face `side` (lo: x = -2,
+ *     -1; hi: x = nx, nx+1) from buf, same layout; the face must be
+ *     LBM_BC_EXTERNAL.  The lo neighbour's hi source is this slab's lo halo,
+ *     the hi neighbour's lo source its hi halo.
+ * With on_device = 1 both are asynchronous on the sim's stream (buf a device
+ * pointer, valid once the stream reaches the call); with on_device = 0 they
+ * stage through the spare f buffer and synchronise.  A sim with EXTERNAL
+ * faces steps one step per lbm_step call, after lbm_set_halo on each of its
+ * EXTERNAL faces since its previous step (LBM_EINVAL otherwise), and is not
+ * taken by lbm_step_batch or lbm_graph_capture.  Errors: LBM_EINVAL (side
+ * not 0 / 1, NULL buf, face not EXTERNAL), LBM_ECUDA. */
+LBM_API int lbm_get_halo_source(lbm_sim* sim, int32_t side, void* buf, int32_t on_device);
+LBM_API int lbm_set_halo(lbm_sim* sim, int32_t side, const void* buf, int32_t on_device);
 
 /* Synchronise and read the health flag bits (LBM_HEALTH_*) accumulated since
  * lbm_init; returns LBM_ETIMEOUT when a bounded device wait ran out

@@ -12,7 +12,7 @@ import threading
 from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ESTATE = 0, -1, -2, -3, -4, -5, -6
-LBM_BC_PERIODIC, LBM_BC_FIXED, LBM_BC_EXTRAPOLATE, LBM_BC_REFLECT = 0, 1, 2, 3
+LBM_BC_PERIODIC, LBM_BC_FIXED, LBM_BC_EXTRAPOLATE, LBM_BC_REFLECT, LBM_BC_EXTERNAL = 0, 1, 2, 3, 4
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_SCHEME_NND, LBM_SCHEME_UPWIND2, LBM_SCHEME_UPWIND1 = 0, 1, 2
 LBM_HEALTH_NONFINITE, LBM_HEALTH_RHO, LBM_HEALTH_T, LBM_HEALTH_TIMEOUT = 1, 2, 4, 8
@@ -63,6 +63,8 @@ SIGNATURES = [
     ("lbm_conserved", ctypes.c_int, [_vp, _dp]),
     ("lbm_conserved_noalloc", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(lbm_vset), _vp, ctypes.c_int32, _vp]),
+    ("lbm_get_halo_source", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32]),
+    ("lbm_set_halo", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32]),
     ("lbm_health", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     ("lbm_sync", ctypes.c_int, [_vp]),
     ("lbm_steps_done", ctypes.c_int64, [_vp]),
@@ -131,6 +133,8 @@ lbm_get_f = _forward("lbm_get_f")
 lbm_set_f = _forward("lbm_set_f")
 lbm_conserved = _forward("lbm_conserved")
 lbm_conserved_noalloc = _forward("lbm_conserved_noalloc")
+lbm_get_halo_source = _forward("lbm_get_halo_source")
+lbm_set_halo = _forward("lbm_set_halo")
 lbm_health = _forward("lbm_health")
 lbm_sync = _forward("lbm_sync")
 lbm_steps_done = _forward("lbm_steps_done")

@@ -182,6 +182,25 @@ __global__ void unpack_kernel(R* __restrict__ f, Layout L, const R* __restrict__
   for (int i = 0; i < NV; ++i) f[i * L.fs + idx] = dense[i * n + k];
 }
 
+// Two x-columns of every (y, z) row and field against a dense [15][nz][ny][2]
+// array: to_dense = 1 copies the interior columns next to the x face `side`
+// (x = 0, 1 or nx-2, nx-1) out, to_dense = 0 writes the two layers outside it
+// (x = -2, -1 or nx, nx+1).  One thread per (field, row, column).
+template <typename R>
+__global__ void halo_kernel(R* __restrict__ f, Layout L, int side, int to_dense, R* __restrict__ dense) {
+  const long long rows = (long long)L.ny * L.nz;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= rows * 2 * NV) return;
+  const int j = (int)(k & 1);
+  const long long r = (k >> 1) % rows;
+  const int i = (int)((k >> 1) / rows);
+  const int y = (int)(r % L.ny), z = (int)(r / L.ny);
+  const int x = to_dense ? (side ? L.nx - 2 + j : j) : (side ? L.nx + j : -2 + j);
+  const long long at = (long long)i * L.fs + L.at(x, y, z);
+  if (to_dense) dense[k] = f[at];
+  else f[at] = dense[k];
+}
+
 // conservation sums: blocks of 12 warps, 4 row slots x 3 groups of 5 fields
 constexpr int RED_GROUPS = 3, RED_GF = NV / RED_GROUPS, RED_ROWS = 4;
 constexpr int RED_THREADS = 32 * RED_GROUPS * RED_ROWS;
@@ -386,6 +405,13 @@ cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense,
   const int b = blocks_for(L.ncell(), 256);
   if (prec == LBM_FP64) unpack_kernel<double><<<b, 256, 0, st>>>((double*)f, L, (const double*)dense);
   else unpack_kernel<float><<<b, 256, 0, st>>>((float*)f, L, (const float*)dense);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo(int prec, void* f, const Layout& L, int side, int to_dense, void* dense, cudaStream_t st) {
+  const int b = blocks_for((long long)L.ny * L.nz * 2 * NV, 256);
+  if (prec == LBM_FP64) halo_kernel<double><<<b, 256, 0, st>>>((double*)f, L, side, to_dense, (double*)dense);
+  else halo_kernel<float><<<b, 256, 0, st>>>((float*)f, L, side, to_dense, (float*)dense);
   return cudaGetLastError();
 }
 

@@ -39,8 +39,9 @@ bool grid_ok(const lbm_grid* g) {
   for (int a = 0; a < 3; ++a) {
     for (int h = 0; h < 2; ++h) {
       const int k = h ? g->bc_hi[a] : g->bc_lo[a];
-      if (k < LBM_BC_PERIODIC || k > LBM_BC_REFLECT) return false;
-      if (k == LBM_BC_EXTRAPOLATE && n[a] < 2) return false;
+      if (k < LBM_BC_PERIODIC || k > LBM_BC_EXTERNAL) return false;
+      if ((k == LBM_BC_EXTRAPOLATE || k == LBM_BC_EXTERNAL) && n[a] < 2) return false;
+      if (k == LBM_BC_EXTERNAL && a != 0) return false;  // slabs are cut along x
     }
     if ((g->bc_lo[a] == LBM_BC_PERIODIC) != (g->bc_hi[a] == LBM_BC_PERIODIC)) return false;
   }
@@ -157,6 +158,8 @@ struct lbm_sim {
   cudaStream_t st;
   int64_t steps;
   int failed;
+  unsigned external;    // faces (bit 2*axis+hi) whose layers the caller supplies (LBM_BC_EXTERNAL)
+  unsigned halo_set;    // EXTERNAL faces written by lbm_set_halo since the last step
   int fixed_dirty[2];   // FIXED-face layers of buffer b need rewriting
   int layers_ok[2];     // buffer b's non-FIXED boundary layers match its interior
   unsigned wait_limit;  // polls of a TMA data wait before the step kernel gives up
@@ -322,11 +325,16 @@ int auto_ztail(int zc) { return zc >= 12 ? 8 : 0; }
 unsigned step_faces(const lbm_sim* s) {
   unsigned m = 0;
   for (int f = 0; f < 6; ++f)
-    if (s->bc.kind[f] != LBM_BC_FIXED) m |= 1u << f;
+    if (s->bc.kind[f] != LBM_BC_FIXED && s->bc.kind[f] != LBM_BC_EXTERNAL) m |= 1u << f;
   return m;
 }
 
-unsigned fixed_faces(const lbm_sim* s) { return 0x3fu & ~step_faces(s); }
+unsigned fixed_faces(const lbm_sim* s) {
+  unsigned m = 0;
+  for (int f = 0; f < 6; ++f)
+    if (s->bc.kind[f] == LBM_BC_FIXED) m |= 1u << f;
+  return m;
+}
 
 // Boundary layers the pair kernel writes for the state it produces, and the
 // face mask they cover: periodic axes (x only for even nx, where the boundary
@@ -428,6 +436,10 @@ int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt
       s->bc.fixed[2 * a + 1][k] = grid->fixed_hi[a][k];
     }
   }
+  s->external = 0;
+  for (int f = 0; f < 6; ++f)
+    if (s->bc.kind[f] == LBM_BC_EXTERNAL) s->external |= 1u << f;
+  s->halo_set = 0;
   s->ws = (char*)d_workspace;
   s->ws_bytes = ws_bytes;
   const size_t fb = field_bytes(s->L, s->esz);
@@ -610,6 +622,7 @@ int batch_check(lbm_sim* const* sims, int32_t n) {
     if (!s) return LBM_EINVAL;
     if (s->failed) return LBM_ESTATE;
     if (s->prec != LBM_FP32 || !wt_variant(s->variant) || s->variant != sims[0]->variant) return LBM_EINVAL;
+    if (s->external) return LBM_EINVAL;  // slab sims step one at a time between halo exchanges
     if (s->scheme != sims[0]->scheme || s->st != sims[0]->st || s->device != sims[0]->device) return LBM_EINVAL;
     for (int j = 0; j < i; ++j)
       if (sims[j] == s) return LBM_EINVAL;
@@ -695,7 +708,46 @@ int lbm_step(lbm_sim* s, int64_t n) {
   int rc = enter(s);
   if (rc) return rc;
   if (n < 0) return LBM_EINVAL;
+  if (s->external && n > 0) {
+    // the caller's layers are one step's worth: one step at a time, each after its lbm_set_halo calls
+    if (n != 1 || (s->halo_set & s->external) != s->external) return LBM_EINVAL;
+    s->halo_set = 0;
+  }
   return run_steps(s, n);
+}
+
+int lbm_get_halo_source(lbm_sim* s, int32_t side, void* buf, int32_t on_device) {
+  int rc = enter(s);
+  if (rc) return rc;
+  if (!buf || (side != 0 && side != 1) || s->L.nx < 2) return LBM_EINVAL;
+  const size_t bytes = (size_t)lbm::NV * s->L.ny * s->L.nz * 2 * s->esz;
+  if (on_device) {
+    LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_halo(s->prec, s->fbuf[s->cur], s->L, side, 1, buf, s->st));
+    return LBM_OK;
+  }
+  void* stg = spare(s);
+  LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_halo(s->prec, s->fbuf[s->cur], s->L, side, 1, stg, s->st));
+  LBM_CK(s, cudaMemcpyAsync(buf, stg, bytes, cudaMemcpyDeviceToHost, s->st));
+  LBM_CK(s, cudaStreamSynchronize(s->st));
+  return LBM_OK;
+}
+
+int lbm_set_halo(lbm_sim* s, int32_t side, const void* buf, int32_t on_device) {
+  int rc = enter(s);
+  if (rc) return rc;
+  if (!buf || (side != 0 && side != 1) || !((s->external >> side) & 1u)) return LBM_EINVAL;
+  const size_t bytes = (size_t)lbm::NV * s->L.ny * s->L.nz * 2 * s->esz;
+  if (on_device) {
+    LBM_LAUNCH(s, LBM_KERNEL_OTHER,
+               lbm::launch_halo(s->prec, s->fbuf[s->cur], s->L, side, 0, const_cast<void*>(buf), s->st));
+  } else {
+    void* stg = spare(s);
+    LBM_CK(s, cudaMemcpyAsync(stg, buf, bytes, cudaMemcpyHostToDevice, s->st));
+    LBM_LAUNCH(s, LBM_KERNEL_OTHER, lbm::launch_halo(s->prec, s->fbuf[s->cur], s->L, side, 0, stg, s->st));
+    LBM_CK(s, cudaStreamSynchronize(s->st));
+  }
+  s->halo_set |= 1u << side;
+  return LBM_OK;
 }
 
 int lbm_step_batch(lbm_sim* const* sims, int32_t n, int64_t steps) {
@@ -712,7 +764,7 @@ int lbm_graph_capture(lbm_sim* const* sims, int32_t n, int64_t steps, lbm_graph*
   if (!out) return LBM_EINVAL;
   *out = nullptr;
   if (!sims || n < 1 || steps < 2 || steps % 2) return LBM_EINVAL;
-  int rc = n == 1 ? (sims[0] ? LBM_OK : LBM_EINVAL) : batch_check(sims, n);
+  int rc = n == 1 ? (sims[0] ? (sims[0]->external ? LBM_EINVAL : LBM_OK) : LBM_EINVAL) : batch_check(sims, n);
   if (rc) return rc;
   lbm_sim* s0 = sims[0];
   rc = enter(s0);

@@ -206,6 +206,9 @@ cudaError_t launch_moments(int prec, const void* f, const Layout& L, const Model
                            double* T, cudaStream_t st);
 cudaError_t launch_pack(int prec, const void* f, const Layout& L, void* dense, cudaStream_t st);
 cudaError_t launch_unpack(int prec, void* f, const Layout& L, const void* dense, cudaStream_t st);
+// The two x-columns next to (to_dense = 1) or outside (to_dense = 0) the x
+// face `side` (0 lo, 1 hi) against dense [15][nz][ny][2] (x order).
+cudaError_t launch_halo(int prec, void* f, const Layout& L, int side, int to_dense, void* dense, cudaStream_t st);
 cudaError_t launch_conserved(int prec, const void* f, const Layout& L, const Model<double>& m, double* partials,
                              int max_blocks, unsigned* counter, double* result, unsigned* flags, cudaStream_t st);
 cudaError_t launch_step_plain(int prec, int scheme, const void* fin, void* fout, const Layout& L,

@@ -154,6 +154,31 @@ class Sim:
         A.check(A.lbm_moments(self._h, _ptr(rho), _ptr(u), _ptr(T), 0), "lbm_moments")
         return rho, u, T
 
+    # -- x slabs (slabs.py) ------------------------------------------------------
+    def halo_source(self, side: int, out=None) -> torch.Tensor:
+        """The two interior x-columns next to x face `side` (0 lo, 1 hi) of the
+        current state as a CUDA tensor [15, nz, ny, 2] in the storage precision
+        (lbm_get_halo_source; asynchronous on the sim's stream)."""
+        nz, ny, _ = self.shape
+        if out is None:
+            out = torch.empty((15, nz, ny, 2), device=self.device,
+                              dtype=torch.float64 if self.dtype == np.float64 else torch.float32)
+        A.check(A.lbm_get_halo_source(self._h, int(side), _ptr(out), 1), "lbm_get_halo_source")
+        return out
+
+    def set_halo(self, side: int, buf):
+        """The two layers outside the EXTERNAL x face `side` from buf
+        ([15, nz, ny, 2]; a CUDA tensor: asynchronous on the sim's stream,
+        kept alive until the next call; else a host array: synchronous)."""
+        if isinstance(buf, torch.Tensor) and buf.is_cuda:
+            b = buf.contiguous()
+            A.check(A.lbm_set_halo(self._h, int(side), _ptr(b), 1), "lbm_set_halo")
+            self._halo_keep = getattr(self, "_halo_keep", {})
+            self._halo_keep[int(side)] = b
+        else:
+            b = np.ascontiguousarray(buf.numpy() if isinstance(buf, torch.Tensor) else buf, dtype=self.dtype)
+            A.check(A.lbm_set_halo(self._h, int(side), _ptr(b), 0), "lbm_set_halo")
+
     def get_f(self, out=None) -> np.ndarray:
         """Interior f, [15, nz, ny, nx], in the storage precision (host copy,
         or into ``out`` when it is a CUDA tensor of that shape and dtype)."""

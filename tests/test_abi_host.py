@@ -132,3 +132,19 @@ def test_build_fails_loudly_without_nvcc(monkeypatch):
     monkeypatch.setattr(build.os.path, "exists", lambda p: False)
     with pytest.raises(RuntimeError, match="nvcc not found"):
         build.nvcc()
+
+
+def test_external_faces_are_x_faces_of_two_cells_or_more(A):
+    g = A.make_grid(8, 6, 5, (A.LBM_BC_EXTERNAL, 0, 3), (A.LBM_BC_EXTERNAL, 0, 3))
+    assert A.lbm_workspace_bytes(ctypes.byref(g), A.LBM_FP32) > 0
+    for lo, hi in (((0, A.LBM_BC_EXTERNAL, 0), (0, A.LBM_BC_EXTERNAL, 0)),   # y faces: no
+                   ((1, 0, A.LBM_BC_EXTERNAL), (1, 0, 3)),                   # z face: no
+                   ((5, 0, 0), (1, 0, 0))):                                   # unknown kind
+        assert A.lbm_workspace_bytes(ctypes.byref(A.make_grid(8, 6, 5, lo, hi)), A.LBM_FP32) == 0
+    assert A.lbm_workspace_bytes(ctypes.byref(A.make_grid(1, 6, 5, (A.LBM_BC_EXTERNAL, 0, 0), (1, 0, 0))),
+                                 A.LBM_FP32) == 0
+
+
+def test_every_bound_entry_point_has_a_forwarder(A):
+    for n, _, _ in A.SIGNATURES:
+        assert callable(getattr(A, n, None)), n
