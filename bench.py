@@ -42,8 +42,12 @@ def parse():
     p.add_argument("--rate", type=float, default=20.0, help="serve: mean arrival rate (requests/s)")
     p.add_argument("--hbm-budget-gb", type=float, default=0.0, help="serve: workspace budget (0 = 80%% of free)")
     p.add_argument("--policy", default="fifo", choices=["fifo", "sjf"], help="serve: admission order")
-    p.add_argument("--l1-sample", type=float, default=0.0,
-                   help="serve: fraction of requests (seeded) checked against the FP64 path (0 = the three smallest)")
+    p.add_argument("--l1-sample", type=float, default=0.1,
+                   help="serve: fraction of the finished requests (seeded) checked against the FP64 path")
+    p.add_argument("--serve-requests", type=int, default=30,
+                   help="default line: requests of the compact serving summary (0 = none)")
+    p.add_argument("--serve-rate", type=float, default=2.0,
+                   help="default line: arrival rate of the compact serving summary (the sustainable rate)")
     p.add_argument("--workload", default="droplet", choices=["droplet", "bubble", "batch", "batch_small", "serve"],
                    help="droplet: 256^3 Mach-2 shock-droplet; bubble: 512x256x256 Mach-3 shock-bubble; "
                         "batch: the bubble grid plus 8 128^3 copies with seeded Mach numbers, one launch per "
@@ -117,6 +121,16 @@ def run_batch(args):
     g = S.Graph(sims, gsteps)
     g.launch(1)
     torch.cuda.synchronize()
+    # the timed region lasts at least 1.2 s, so that the 200 ms clock samples
+    # number at least five
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(sims[0].stream)
+    g.launch(1)
+    e1.record(sims[0].stream)
+    e1.synchronize()
+    per_step_est = e0.elapsed_time(e1) / gsteps
+    steps = max(steps, gsteps * int(-(-1200.0 // (per_step_est * gsteps))))
     clocks = ClockSampler(gpu_smi_id(torch, 0))
     time.sleep(0.5)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -481,6 +495,13 @@ def run_ours(args):
                 "traffic": recorded_traffic("step", args.precision, w.ncell),
                 "avg_launch_ms": avg_step_s * 1e3, "fill_avg_launch_ms": fill_ms / max(1, fill_n)}
 
+    serving = None
+    if args.serve_requests > 0 and world == 1 and args.precision == "fp32":
+        s.close()
+        torch.cuda.empty_cache()
+        stats, srv, _, errors, sclock = serve_trace(args.serve_requests, args.serve_rate, "fifo", 0.1)
+        serving = serving_summary(stats, errors, sclock, args.serve_requests, args.serve_rate, srv)
+
     cpu = None
     if not args.no_cpu and world == 1:
         rate, cores, ww, dt = cpu_oracle_rate(w, args.cpu_steps)
@@ -503,6 +524,7 @@ def run_ours(args):
                               "tune_timings_ms": tuned.get("timings") if tuned else None}},
         "roofline": roofline,
         "accuracy": accuracy,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(step_n + fill_n) * world,
@@ -515,32 +537,33 @@ def run_ours(args):
     return 0
 
 
-def run_serve(args):
-    """The seeded Poisson request stream served in real time; reports latency
-    percentiles, throughput and the L1 density error of sampled requests
-    against the FP64 path (parity-checked against the oracle)."""
+def serve_trace(requests, rate, policy="fifo", l1_frac=0.1, budget=None, seed=5):
+    """The seeded Poisson request stream (`requests` arrivals at mean `rate`
+    per second) through the continuous-batching server in real time, with
+    nvidia-smi clocks sampled during it, and the L1 / Linf density error of a
+    seeded fraction l1_frac of the finished requests against the FP64 path
+    (parity-checked against the oracle).  Returns (summary, server, finished
+    jobs, per-request errors, clocks)."""
     import numpy as np
     import torch
     import workloads
     from paper_1010_4135_gb300 import serve
     from paper_1010_4135_gb300 import sim as S
-    torch.cuda.set_device(0)
-    trace = workloads.serving_trace(seed=5, n=args.requests, rate=args.rate)
-    budget = int(args.hbm_budget_gb * 2 ** 30) if args.hbm_budget_gb > 0 else None
-    srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True, policy=args.policy)
+    trace = workloads.serving_trace(seed=seed, n=requests, rate=rate)
+    srv = serve.Server(hbm_budget=budget, tick=50, keep_results=True, policy=policy)
     srv.tune_shapes(workloads.SERVING_GRIDS)  # before the trace starts: the server's grid menu
+    clocks = ClockSampler(gpu_smi_id(torch, torch.cuda.current_device()))
+    t0 = time.time()
     done = srv.run(trace)
+    t1 = time.time()
+    clock = clocks.summary(t0, t1)
+    clocks.stop()
     stats = serve.summary(done, srv.wall)
-    # L1 / Linf of rho against the FP64 path (itself parity-checked against the oracle):
-    # a seeded sample of the finished requests, or the three smallest
-    if args.l1_sample > 0:
-        k = max(1, int(round(args.l1_sample * len(done))))
-        pick = np.random.default_rng(11).choice(len(done), size=k, replace=False)
-        sample = [done[i] for i in sorted(pick)]
-    else:
-        sample = sorted(done, key=lambda j: (int(np.prod(j.req["grid"])) * j.req["steps"], j.req["id"]))[:3]
-    l1 = []
-    for j in sample:
+    k = max(1, int(round(l1_frac * len(done))))
+    pick = np.random.default_rng(11).choice(len(done), size=k, replace=False)
+    errors = []
+    for i in sorted(pick):
+        j = done[i]
         w = workloads.request_workload(j.req, *j.params)
         s = S.from_workload(w, precision="fp64")
         rho, u, T = w.initial_fields()
@@ -548,10 +571,41 @@ def run_serve(args):
         s.step(j.req["steps"])
         r64, _, _ = s.moments()
         s.close()
-        l1.append({"id": j.req["id"], "kind": j.req["kind"], "grid": list(j.req["grid"]), "steps": j.req["steps"],
-                   "mach": j.req["mach"], "ratio": j.req["ratio"], "health": j.health,
-                   "l1_rho": float(np.abs(j.rho - r64).sum() / np.abs(r64).sum()),
-                   "linf_rho": float(np.abs(j.rho - r64).max() / np.abs(r64).max())})
+        errors.append({"id": j.req["id"], "kind": j.req["kind"], "grid": list(j.req["grid"]), "steps": j.req["steps"],
+                       "mach": j.req["mach"], "ratio": j.req["ratio"], "health": j.health,
+                       "l1_rho": float(np.abs(j.rho - r64).sum() / np.abs(r64).sum()),
+                       "linf_rho": float(np.abs(j.rho - r64).max() / np.abs(r64).max())})
+    return stats, srv, done, errors, clock
+
+
+def serving_summary(stats, errors, clock, requests, rate, srv):
+    """The compact serving object of a bench line."""
+    l1 = [e["l1_rho"] for e in errors]
+    linf = [e["linf_rho"] for e in errors]
+    return {"trace": f"{requests} requests, Poisson rate {rate}/s (seed 5), grids 64^3..256^3, Mach U[1.2,10], "
+                     "density ratio log-U[0.1,10], 500-3000 steps, FP32",
+            "admission": srv.policy, "p50_latency_s": stats["p50_latency_s"], "p99_latency_s": stats["p99_latency_s"],
+            "solves_per_s": stats["solves_per_s"], "cell_updates_per_s": stats["cell_updates_per_s"],
+            "unhealthy": stats["unhealthy"], "retried": stats["retried"],
+            "l1_rho_vs_fp64": {"sample": f"seeded {len(errors)} of {stats['requests']} finished requests",
+                               "median": float(statistics.median(l1)), "max": max(l1),
+                               "linf_max": max(linf)},
+            "parameter_rule": "on the device (lbm_vn_max_growth)" if srv.vn_device else "on the host",
+            "preparation_s_per_request": {k: v / max(1, srv.prep_s.get("requests", 0))
+                                          for k, v in srv.prep_s.items() if k != "requests"},
+            "clocks": clock}
+
+
+def run_serve(args):
+    """The seeded Poisson request stream served in real time; reports latency
+    percentiles, throughput, clocks and the L1 density error of a seeded
+    sample of requests against the FP64 path (parity-checked against the
+    oracle)."""
+    import torch
+    torch.cuda.set_device(0)
+    budget = int(args.hbm_budget_gb * 2 ** 30) if args.hbm_budget_gb > 0 else None
+    frac = args.l1_sample if args.l1_sample > 0 else 0.1
+    stats, srv, done, l1, clock = serve_trace(args.requests, args.rate, args.policy, frac, budget)
     line = {
         "metric": METRIC, "value": stats["cell_updates_per_s"], "unit": UNIT, "n_gpus": 1,
         "steps": int(sum(j.req["steps"] for j in done)), "warmup": 0,
@@ -561,9 +615,10 @@ def run_serve(args):
                                "64^3..256^3, Mach U[1.2,10], density ratio log-U[0.1,10], 500-3000 steps, FP32",
                    "admission": srv.policy, "hbm_budget_bytes": srv.budget, "peak_resident_bytes": srv.peak_bytes,
                    "peak_batch": srv.peak_batch, "host_seconds": dict(srv.host_s),
-                   "l1_sample": (f"seeded {args.l1_sample:.0%} of the finished requests" if args.l1_sample > 0
-                                 else "the three smallest finished requests")},
-        "serving": stats, "l1_vs_fp64_sample": l1, "gpu_launches": srv.launches,
+                   "preparation_seconds": dict(srv.prep_s),
+                   "parameter_rule": "on the device (lbm_vn_max_growth)" if srv.vn_device else "on the host",
+                   "l1_sample": f"seeded {frac:.0%} of the finished requests"},
+        "serving": stats, "l1_vs_fp64_sample": l1, "gpu_launches": srv.launches, "clocks": clock,
         "unhealthy_requests": [{"id": j.req["id"], "kind": j.req["kind"], "grid": list(j.req["grid"]),
                                 "mach": j.req["mach"], "ratio": j.req["ratio"], "c1_c2_eta0_dt": list(j.params),
                                 "health": j.health} for j in done if j.health],

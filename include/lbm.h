@@ -239,6 +239,23 @@ LBM_API int lbm_conserved_noalloc(const void* f, int32_t precision, int32_t nx, 
 LBM_API int lbm_get_halo_source(lbm_sim* sim, int32_t side, void* buf, int32_t on_device);
 LBM_API int lbm_set_halo(lbm_sim* sim, int32_t side, const void* buf, int32_t on_device);
 
+/* Von Neumann stability (Sec. 3): for each parameter set p, out[p] = the
+ * largest spectral radius max |omega| of the amplification matrix G(k) of one
+ * step (the paper's G with alpha~ = beta~ = 0: first-order upwind phases,
+ * BGK relaxation, the extra dissipation term when dissipation = 1, and the
+ * equilibrium Jacobian by the chain rule through rho, u and T) over the
+ * uniform states, the wave-vector directions and the wave numbers
+ * |k| dx = pi q / nk, q = 1..nk.  states: nstates x (rho, u1, u2, u3, T);
+ * params: nparams x (c1, c2, eta0, gamma, dt, tau, dx); dirs: ndirs x 3
+ * (normalised here); out: nparams doubles.  All four are device pointers;
+ * asynchronous on cuda_stream.  A matrix whose eigenvalue iteration does not
+ * converge, or that holds non-finite values, gives +inf.  The paper accepts
+ * a scheme when max |omega| <= 1.  Errors: LBM_EINVAL (NULL pointers, counts
+ * < 1, more than 2^30 matrices), LBM_ECUDA. */
+LBM_API int lbm_vn_max_growth(const double* states, int32_t nstates, const double* params, int32_t nparams,
+                              const double* dirs, int32_t ndirs, int32_t nk, int32_t dissipation, double* out,
+                              void* cuda_stream);
+
 /* Synchronise and read the health flag bits (LBM_HEALTH_*) accumulated since
  * lbm_init; returns LBM_ETIMEOUT when a bounded device wait ran out
  * (LBM_HEALTH_TIMEOUT), else LBM_ENONFINITE when any other bit is set. */

@@ -65,6 +65,8 @@ SIGNATURES = [
                                              ctypes.POINTER(lbm_vset), _vp, ctypes.c_int32, _vp]),
     ("lbm_get_halo_source", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32]),
     ("lbm_set_halo", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32]),
+    ("lbm_vn_max_growth", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     ("lbm_health", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     ("lbm_sync", ctypes.c_int, [_vp]),
     ("lbm_steps_done", ctypes.c_int64, [_vp]),
@@ -135,6 +137,7 @@ lbm_conserved = _forward("lbm_conserved")
 lbm_conserved_noalloc = _forward("lbm_conserved_noalloc")
 lbm_get_halo_source = _forward("lbm_get_halo_source")
 lbm_set_halo = _forward("lbm_set_halo")
+lbm_vn_max_growth = _forward("lbm_vn_max_growth")
 lbm_health = _forward("lbm_health")
 lbm_sync = _forward("lbm_sync")
 lbm_steps_done = _forward("lbm_steps_done")

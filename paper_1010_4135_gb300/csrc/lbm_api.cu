@@ -1047,3 +1047,15 @@ void lbm_destroy(lbm_sim* s) {
 }
 
 }  // extern "C"
+
+extern "C" int lbm_vn_max_growth(const double* states, int32_t nstates, const double* params, int32_t nparams,
+                                 const double* dirs, int32_t ndirs, int32_t nk, int32_t dissipation, double* out,
+                                 void* cuda_stream) {
+  if (!states || !params || !dirs || !out || nstates < 1 || nparams < 1 || ndirs < 1 || nk < 1) return LBM_EINVAL;
+  const long long items = (long long)nstates * ndirs * nk * nparams;
+  if (items > (1LL << 30)) return LBM_EINVAL;
+  return lbm::launch_vn_max_growth(states, nstates, params, nparams, dirs, ndirs, nk, dissipation, out,
+                                   (cudaStream_t)cuda_stream) == cudaSuccess
+             ? LBM_OK
+             : LBM_ECUDA;
+}

@@ -33,6 +33,7 @@ import collections
 import concurrent.futures as cf
 import ctypes
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -112,7 +113,19 @@ def note_admission(waiting, job):
         j.bypassed += 1
 
 
-def request_parameters(req, attempt: int = 0):
+_tls = threading.local()
+
+
+def _service_stream():
+    """A CUDA stream of this (preparation) thread for the parameter service."""
+    s = getattr(_tls, "stream", None)
+    if s is None:
+        s = torch.cuda.Stream()
+        _tls.stream = s
+    return s
+
+
+def request_parameters(req, attempt: int = 0, device: bool = False):
     """(c1, c2, eta0, dt) of a request.  Attempt 0: the von Neumann rule
     (stability.choose_parameters) applied to its initial states and to the
     star states where the shocked gas meets the second gas (the tube's
@@ -121,11 +134,14 @@ def request_parameters(req, attempt: int = 0):
     the populations realizable, so attempt 1 takes c1 - 1 (c2 = 3 c1, eta0 =
     2 c1), attempt 2 the rule's c1 with eta0 = c1 (the paper's most common
     choice).  Measured on the seeded 200-request trace: the three requests
-    the rule left unhealthy all finish healthy with attempt 1."""
+    the rule left unhealthy all finish healthy with attempt 1.  device=True
+    measures all candidates in one launch of the on-device von Neumann service
+    (on this thread's own stream)."""
     nx, ny, nz = req["grid"]
     pre, post, other = workloads.request_states(req)
     states = [pre, post, other, *stability.interaction_states(post, other)]
-    c1, c2, eta0, dt = stability.choose_parameters(states, 1.0 / ny)
+    c1, c2, eta0, dt = stability.choose_parameters(states, 1.0 / ny, device=device,
+                                                   stream=_service_stream() if device else None)
     if dt is None:
         dt = min(stability.DT_CANDIDATES)
     if attempt == 1 and c1 > 2.0:
@@ -136,12 +152,18 @@ def request_parameters(req, attempt: int = 0):
     return c1, c2, eta0, dt
 
 
-def prepare(req, attempt: int = 0):
-    """Host work of one request: parameters, workload and initial fields (in
-    page-locked memory, ready for an asynchronous copy)."""
-    params = request_parameters(req, attempt)
+def prepare(req, attempt: int = 0, device: bool = False, timing=None):
+    """Work of one request before admission: parameters (the von Neumann rule,
+    on the device with device=True), workload and initial fields (in
+    page-locked memory, ready for an asynchronous copy).  timing(params_s,
+    fields_s), if given, receives the seconds of the two parts."""
+    t0 = time.perf_counter()
+    params = request_parameters(req, attempt, device)
+    t1 = time.perf_counter()
     w = workloads.request_workload(req, *params)
     fields = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.initial_fields())
+    if timing is not None:
+        timing(t1 - t0, time.perf_counter() - t1)
     return params, w, fields
 
 
@@ -162,7 +184,7 @@ class Server:
     VARIANT = ("tiled",)
 
     def __init__(self, hbm_budget=None, max_batch=A.LBM_MAX_BATCH, tick=50, keep_results=False, tune=True,
-                 prep_workers=2, policy="fifo"):
+                 prep_workers=2, policy="fifo", vn_device=True):
         if policy not in POLICIES:
             raise ValueError(f"policy must be one of {POLICIES}")
         self.policy = policy
@@ -181,6 +203,17 @@ class Server:
         self.launches = 0
         self.retries = 0
         self.host_s = collections.Counter()  # host seconds by activity
+        # request preparation (worker threads): the parameter rule on the device
+        # (vn_device) or the host, and the initial fields
+        self.vn_device = bool(vn_device)
+        self.prep_s = collections.Counter()
+        self._prep_lock = threading.Lock()
+
+    def _note_prep(self, params_s, fields_s):
+        with self._prep_lock:
+            self.prep_s["params"] += params_s
+            self.prep_s["fields"] += fields_s
+            self.prep_s["requests"] += 1
 
     def tune_shapes(self, grids):
         """Autotune each grid shape once before serving (cached per shape)."""
@@ -252,7 +285,8 @@ class Server:
                 h = time.perf_counter()
                 while pending and pending[0]["arrival"] * time_scale <= clock():
                     r = pending.popleft()
-                    waiting.append(Job(req=r, nbytes=workspace_bytes(r["grid"]), prep=pool.submit(prepare, r)))
+                    waiting.append(Job(req=r, nbytes=workspace_bytes(r["grid"]),
+                                       prep=pool.submit(prepare, r, 0, self.vn_device, self._note_prep)))
                 # admission by the policy, footprint and batch slots, once prepared
                 while len(active) < self.max_batch:
                     j = next_admission(waiting, used, self.budget, self.policy)
@@ -287,7 +321,8 @@ class Server:
                             # solve it again with the next parameter candidate, first in line
                             self.retries += 1
                             waiting.appendleft(Job(req=j.req, nbytes=j.nbytes, attempt=j.attempt + 1,
-                                                   prep=pool.submit(prepare, j.req, j.attempt + 1)))
+                                                   prep=pool.submit(prepare, j.req, j.attempt + 1, self.vn_device,
+                                                                   self._note_prep)))
                         else:
                             done.append(j)
                     else:

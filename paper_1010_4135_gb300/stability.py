@@ -15,7 +15,10 @@ w_i = v_i . u, taken from the printed A_i, B_i, D_i.
 
 The scheme is accepted when max |omega| <= 1 + tol over the sampled wave
 numbers (the paper's criterion max |omega| <= 1, read to plotting accuracy).
-Host-side helper for the serving loop; the step itself runs in liblbm.so.
+`max_growth` evaluates G on the host (numpy eigenvalues); `max_growth_device`
+evaluates a whole batch of parameter sets in one launch of liblbm.so's
+lbm_vn_max_growth (G built per thread, Hessenberg QR eigenvalues), and
+`choose_parameters(..., device=True)` uses it for every candidate at once.
 """
 from __future__ import annotations
 
@@ -112,6 +115,33 @@ def max_growth(states, c1, c2, eta0, gamma, dt, tau, dx, nk=48,
     return worst
 
 
+DIRECTIONS = ((1.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+
+
+def max_growth_device(states, param_sets, directions=DIRECTIONS, nk=48, dissipation=True, stream=None):
+    """max |omega| per parameter set (c1, c2, eta0, gamma, dt, tau, dx) over
+    the states, directions and the nk wave numbers k dx = pi q / nk, q = 1..nk
+    (the same samples as max_growth), in one launch of lbm_vn_max_growth on
+    the current CUDA device.  Returns a numpy array (synchronises `stream`)."""
+    import ctypes
+
+    import torch
+
+    from . import _abi as A
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.tensor([[float(x) for x in s] for s in states], dtype=torch.float64, device=dev)
+    ps = torch.tensor([[float(x) for x in p] for p in param_sets], dtype=torch.float64, device=dev)
+    ds = torch.tensor([[float(x) for x in d] for d in directions], dtype=torch.float64, device=dev)
+    out = torch.empty(len(param_sets), dtype=torch.float64, device=dev)
+    stream = stream if stream is not None else torch.cuda.current_stream(dev)
+    A.check(A.lbm_vn_max_growth(ctypes.c_void_p(st.data_ptr()), len(states), ctypes.c_void_p(ps.data_ptr()),
+                                len(param_sets), ctypes.c_void_p(ds.data_ptr()), len(directions), int(nk),
+                                int(bool(dissipation)), ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(stream.cuda_stream)), "lbm_vn_max_growth")
+    stream.synchronize()
+    return out.cpu().numpy()
+
+
 def _velocity_jump(p, rho, pk, gamma):
     """Velocity change across a wave that takes gas (rho, pk) at rest in its
     own frame to pressure p: a shock (Rankine-Hugoniot) when p > pk, an
@@ -170,7 +200,7 @@ def courant(c2: float, dt: float, dx: float) -> float:
 
 
 def choose_parameters(states, dx, gamma=1.4, tol=1e-3, candidates=DT_CANDIDATES, courant_max=COURANT_MAX,
-                      c1_factors=(1.0, 1.1, 1.2, 1.35, 1.5)):
+                      c1_factors=(1.0, 1.1, 1.2, 1.35, 1.5), device=False, stream=None):
     """(c1, c2, eta0, dt) for a run whose fastest material speed is set by the
     given states, following the paper's advice (c1 near the largest flow
     speed, c2 about 3 c1, eta0 1-2 c1): c2 = 3 c1, eta0 = 2 c1, and c1 the
@@ -182,19 +212,29 @@ def choose_parameters(states, dx, gamma=1.4, tol=1e-3, candidates=DT_CANDIDATES,
     interface within tens of steps once c1^2 / T is near 100), and strong
     shocks need the small Courant numbers of the paper's runs (0.01-0.035):
     1D runs of Mach 2-10 shocks stay positive up to 0.05 and fail for some at
-    0.15.  Returns dt = None when no candidate passes."""
+    0.15.  Returns dt = None when no candidate passes.  device=True measures
+    every candidate in one batched launch on the current CUDA device and
+    applies the same rule to the results."""
     umax = max(math.sqrt(sum(float(x) ** 2 for x in st[1:4])) for st in states)
+    order = []  # (c1, dt) in the order the rule tries them
     tried = []
     for f in c1_factors:
         c1 = float(max(2, math.ceil(f * umax)))
         if c1 in tried:
             continue
         tried.append(c1)
-        c2, eta0 = 3.0 * c1, 2.0 * c1
         for dt in sorted(candidates, reverse=True):
-            if courant(c2, dt, dx) > courant_max:
-                continue
-            if max_growth(states, c1, c2, eta0, gamma, dt, dt, dx, nk=24) <= 1.0 + tol:
-                return c1, c2, eta0, dt
+            if courant(3.0 * c1, dt, dx) <= courant_max:
+                order.append((c1, dt))
+    if device and order:
+        g = max_growth_device(states, [(c1, 3.0 * c1, 2.0 * c1, gamma, dt, dt, dx) for c1, dt in order], nk=24,
+                              stream=stream)
+        for (c1, dt), growth in zip(order, g):
+            if growth <= 1.0 + tol:
+                return c1, 3.0 * c1, 2.0 * c1, dt
+    elif not device:
+        for c1, dt in order:
+            if max_growth(states, c1, 3.0 * c1, 2.0 * c1, gamma, dt, dt, dx, nk=24) <= 1.0 + tol:
+                return c1, 3.0 * c1, 2.0 * c1, dt
     c1 = tried[-1]
     return c1, 3.0 * c1, 2.0 * c1, None
