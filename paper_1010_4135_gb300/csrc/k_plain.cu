@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) step_plain_kernel(const R* __restrict__ f
   for (int i = 0; i < NV; ++i) {
     const R* __restrict__ p = fin + i * L.fs + c;
     const R fc = f[i];
-    R conv = R(0), lap = R(0);
+    R conv = R(0), nb = R(0);  // nb: the six neighbours' sum (dissipation, i <= 6)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int sg = vsign(i, a);
@@ -51,20 +51,26 @@ __global__ void __launch_bounds__(256) step_plain_kernel(const R* __restrict__ f
       if (sg > 0) {
         const R m2 = ld(p, -2 * d), m1 = ld(p, -d), p1 = ld(p, d);
         conv += grad_pos<SCHEME>(m2, m1, fc, p1);
-        if (i <= 6) lap += (p1 - R(2) * fc) + m1;
+        if (i <= 6) nb += p1 + m1;
       } else if (sg < 0) {
         const R m1 = ld(p, -d), p1 = ld(p, d), p2 = ld(p, 2 * d);
         conv -= grad_neg<SCHEME>(m1, fc, p1, p2);
-        if (i <= 6) lap += (p1 - R(2) * fc) + m1;
+        if (i <= 6) nb += p1 + m1;
       } else if (i <= 6) {
         const R m1 = ld(p, -d), p1 = ld(p, d);
-        lap += (p1 - R(2) * fc) + m1;
+        nb += p1 + m1;
       }
     }
     const R k = i == 0 ? R(0) : (i <= 6 ? m.k1 : m.k2);
     const R lam = i == 0 ? m.lam0 : (i <= 6 ? m.lam1 : R(0));
-    // conv holds sum_a sign(v_ia) * grad; the velocity magnitude is in k
-    fout[i * L.fs + c] = fc + m.dt_tau * (feq[i] - fc) - k * conv + lam * lap;
+    // f + dt/tau (f^eq - f) - (|v| dt/dx) conv + (lambda dt/dx^2)(nb - 6 f), with the
+    // relaxation and the Laplacian's centre folded into keep = 1 - dt/tau - 6 lambda dt/dx^2;
+    // conv holds sum_a sign(v_ia) * grad, the velocity magnitude is in k
+    const R keep = i == 0 ? m.keep0 : (i <= 6 ? m.keep1 : m.keep2);
+    R o = keep * fc + m.dt_tau * feq[i];
+    if (i != 0) o -= k * conv;
+    if (i <= 6) o += lam * nb;
+    fout[i * L.fs + c] = o;
   }
 }
 

@@ -176,22 +176,33 @@ __device__ __forceinline__ float minmod(float a, float b) {
   return fmaxf(fminf(a, b), 0.0f) + fminf(fmaxf(a, b), 0.0f);
 }
 
+// minmod(x, d) as x clamped to [min(d, 0), max(d, 0)] (exact, like the
+// two-sided form); the two minmods of one cell share d, so its bounds are
+// formed once.
+template <typename R>
+__device__ __forceinline__ R clamp_mm(R x, R lo, R hi) {
+  return fmin(fmax(x, lo), hi);
+}
+
 // dx * d(v f)/dx / v along one axis, from the upwind-side stencil:
 // v > 0 uses f at I-2..I+1 (m2, m1, c, p1); v < 0 uses I-1..I+2 (m1, c, p1, p2).
-// NND: (h_{I+1/2} - h_{I-1/2}) / v with the limited fluxes of Sec. 3.
+// NND: (h_{I+1/2} - h_{I-1/2}) / v with the limited fluxes of Sec. 3; both
+// minmods of the cell take the middle difference as their clamp.
 template <int SCHEME, typename R>
 __device__ __forceinline__ R grad_pos(R m2, R m1, R c, R p1) {
   if (SCHEME == LBM_SCHEME_UPWIND1) return c - m1;
   if (SCHEME == LBM_SCHEME_UPWIND2) return R(0.5) * ((R(3) * c - R(4) * m1) + m2);
   const R d0 = c - m1;
-  return d0 + R(0.5) * (minmod(p1 - c, d0) - minmod(d0, m1 - m2));
+  const R lo = fmin(d0, R(0)), hi = fmax(d0, R(0));
+  return d0 + R(0.5) * (clamp_mm(p1 - c, lo, hi) - clamp_mm(m1 - m2, lo, hi));
 }
 template <int SCHEME, typename R>
 __device__ __forceinline__ R grad_neg(R m1, R c, R p1, R p2) {
   if (SCHEME == LBM_SCHEME_UPWIND1) return p1 - c;
   if (SCHEME == LBM_SCHEME_UPWIND2) return R(0.5) * ((R(4) * p1 - R(3) * c) - p2);
   const R d1 = p1 - c;
-  return d1 - R(0.5) * (minmod(d1, p2 - p1) - minmod(c - m1, d1));
+  const R lo = fmin(d1, R(0)), hi = fmax(d1, R(0));
+  return d1 - R(0.5) * (clamp_mm(p2 - p1, lo, hi) - clamp_mm(c - m1, lo, hi));
 }
 
 // ---------------------------------------------------------------- launchers
