@@ -101,8 +101,10 @@ __device__ __forceinline__ bool half_sync_or(unsigned id, bool v) {
 // Plane j of the unit is the ring's plane number jb + j (slot (jb+j) % NSLOT,
 // phase parity ((jb+j) / NSLOT) & 1), so consecutive units of a CTA keep
 // using the same barriers; jb advances by the unit's plane count.  All
-// threads of the CTA call it together; timed_out is uniform.
-template <int SCHEME, bool WT, class G>
+// threads of the CTA call it together; timed_out is uniform.  FULL: every
+// tile lies inside the grid (nx and ny multiples of the tile), so every pair
+// is active and the activity tests fold away.
+template <int SCHEME, bool WT, class G, bool FULL = false>
 __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* __restrict__ fin,
                                           float* __restrict__ fout, const Layout& L, const Model<float>& m,
                                           const WtDesc& wt, const RecoverDesc& rd, int x0, int y0, int z0,
@@ -113,8 +115,8 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   const int tid = threadIdx.x;
   const int tx = G::col(tid), ty = G::row(tid);
   const int x = x0 + 2 * tx, y = y0 + ty;
-  const bool act0 = (x < L.nx) && (y < L.ny);
-  const bool act1 = (x + 1 < L.nx) && (y < L.ny);
+  const bool act0 = FULL || ((x < L.nx) && (y < L.ny));
+  const bool act1 = FULL || ((x + 1 < L.nx) && (y < L.ny));
   // ring planes 0 .. nzc+1 are the padded planes z0+2 .. z0+nzc+3 (interior
   // z0 .. z0+nzc+1); cell plane k reads ring planes k, k+1, k+2
   const int nplanes = nzc + 2;
@@ -176,31 +178,49 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     for (int i = 0; i < NV; ++i) carry[i] = pm::carry0(i, h2[i], h1[i], ld2(P0 + i * PL + c), ld2(P1 + i * PL + c));
   }
 
-  // F: the own pair of cell plane k; Fn: that of plane k+1, read as the z
-  // neighbour during plane k and kept in registers for the next plane
-  float2 F[NV], Fn[NV];
-  if (!timed_out) {
+  // The own pair of plane k is read from its plane tile at the start of the
+  // plane; the planes below are carried in registers only where a field
+  // needs them: h1 for the Laplacian of f_0..f_6 and the z stencil of the
+  // axis velocities, the lower z difference (dz) for the diagonal velocities
+  // with v_z > 0 (NND), and h2 for the second-order upwind scheme.
+  constexpr bool DZ = SCHEME == LBM_SCHEME_NND;
+  float2 dz[NV];
+  if (!timed_out && DZ) {
     const float* Q0 = slot(0);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) F[i] = ld2(Q0 + i * PL + c);
+    for (int i = 7; i < NV; ++i)
+      if (vsign(i, 2) > 0) dz[i] = pm::sub(ld2(Q0 + i * PL + c), h1[i]);
   }
+  // health: running minima of rho and T and a running sum of the macroscopic
+  // values of each cell of the pair (a non-finite value makes the sum
+  // non-finite), judged once at the end of the unit
+  float2 hmin_rho = make_float2(INFINITY, INFINITY), hmin_T = hmin_rho, hsum = make_float2(0.f, 0.f);
+  // write-through targets that do not depend on the plane: the periodic y and
+  // x images of this pair (element offsets from its own index, 0 = none)
+  long long img_y = 0, img_x = 0;
+  if (WT && act0) {
+    if (wt.per[1]) img_y = y < 2 ? (long long)L.ny * L.sx : (y >= L.ny - 2 ? -(long long)L.ny * L.sx : 0);
+    if (wt.per[0]) img_x = x == 0 ? L.nx : (x == L.nx - 2 ? -L.nx : 0);
+  }
+  const bool face_lo = WT && act0 && wt.xlo && x == 0, face_hi = WT && act0 && wt.xhi && x == L.nx - 2;
   for (int k = 0; k < nzc && !timed_out; ++k) {
     const float* P0 = slot(k);
     const float* P1 = slot(k + 1);
     const float* P2 = slot(k + 2);
-
+    float2 F[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) F[i] = ld2(P0 + i * PL + c);
 
     // moments (relations e1-e3), health, equilibrium and the per-field update
     const pm::Mom r = pm::moments(m, rd, F, P0, c, PL, act0, act1);
-    bad |= pm::health(r, act0, act1);
+    hmin_rho = make_float2(fminf(hmin_rho.x, r.rho.x), fminf(hmin_rho.y, r.rho.y));
+    hmin_T = make_float2(fminf(hmin_T.x, r.T.x), fminf(hmin_T.y, r.T.y));
+    hsum = pm::add(hsum, pm::add(pm::add(r.rho, r.T), pm::add(pm::add(r.ux, r.uy), r.uz)));
     float2 out[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      const float2 Z1 = ld2(P1 + i * PL + c);
-      Fn[i] = Z1;
-      out[i] = pm::field_update<SCHEME, BX>(m, i, P0 + i * PL + c, F[i], Z1, P2 + i * PL + c, h1[i], h2[i],
-                                            carry[i], pm::feq(m, r, i));
-    }
+    for (int i = 0; i < NV; ++i)
+      out[i] = pm::field_update<SCHEME, BX, DZ>(m, i, P0 + i * PL + c, F[i], ld2(P1 + i * PL + c), P2 + i * PL + c,
+                                                h1[i], h2[i], carry[i], dz[i], pm::feq(m, r, i));
     const long long g = gbase + (long long)k * L.plane;
     if (act1) {
 #pragma unroll
@@ -213,15 +233,14 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     // periodic image per axis (axes of >= 4 cells), and the x-face layers
     if (WT && act0) {
       const int z = z0 + k;
-      long long ay = -1, az = -1, ax = -1;
-      if (wt.per[1]) ay = y < 2 ? L.at(x, y + L.ny, z) : (y >= L.ny - 2 ? L.at(x, y - L.ny, z) : -1);
-      if (wt.per[2]) az = z < 2 ? L.at(x, y, z + L.nz) : (z >= L.nz - 2 ? L.at(x, y, z - L.nz) : -1);
-      if (wt.per[0]) ax = x == 0 ? L.at(L.nx, y, z) : (x == L.nx - 2 ? L.at(-2, y, z) : -1);
-      if (ay >= 0 || az >= 0 || ax >= 0) {
+      long long img_z = 0;
+      if (wt.per[2]) img_z = z < 2 ? (long long)L.nz * L.plane : (z >= L.nz - 2 ? -(long long)L.nz * L.plane : 0);
+      if (img_y | img_z | img_x) {
 #pragma unroll 1
         for (int q = 0; q < 3; ++q) {
-          const long long at = q == 0 ? ay : (q == 1 ? az : ax);
-          if (at < 0) continue;
+          const long long off = q == 0 ? img_y : (q == 1 ? img_z : img_x);
+          if (off == 0) continue;
+          const long long at = g + off;
           if (act1) {
 #pragma unroll
             for (int i = 0; i < NV; ++i) *reinterpret_cast<float2*>(fout + i * L.fs + at) = out[i];
@@ -231,11 +250,10 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
           }
         }
       }
-      const bool lo = wt.xlo && x == 0, hi = wt.xhi && x == L.nx - 2;
-      if (lo || hi) {
+      if (face_lo || face_hi) {
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-          if (side == 0 ? !lo : !hi) continue;
+          if (side == 0 ? !face_lo : !face_hi) continue;
           float c0[NV], c1[NV], g1[NV], g2[NV];
 #pragma unroll
           for (int i = 0; i < NV; ++i) {
@@ -253,9 +271,8 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     }
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      h2[i] = h1[i];
+      if (SCHEME == LBM_SCHEME_UPWIND2) h2[i] = h1[i];
       h1[i] = F[i];
-      F[i] = Fn[i];
     }
     // ring plane k+3 (needed next step) must have landed; the barrier also
     // marks plane k as retired, so its slot takes plane k + NSLOT
@@ -291,6 +308,17 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   // releasing slots, so the other one's waits run out too): rejoin here
   if (G::SPLIT) timed_out = __syncthreads_or(timed_out) != 0;
 
+  if (nzc > 0 && !timed_out) {
+    const float mr[2] = {hmin_rho.x, hmin_rho.y}, mt[2] = {hmin_T.x, hmin_T.y}, hs[2] = {hsum.x, hsum.y};
+    const bool on[2] = {act0, act1};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!on[h]) continue;
+      if (!(mr[h] > 0.f)) bad |= LBM_HEALTH_RHO;
+      if (!(mt[h] > 0.f)) bad |= LBM_HEALTH_T;
+      if (!(fabsf(hs[h]) < 1e30f)) bad |= LBM_HEALTH_NONFINITE;
+    }
+  }
   if (tid == 0 && timed_out) atomicOr(flags, (unsigned)LBM_HEALTH_TIMEOUT);
   if (bad) atomicOr(flags, bad);
   if (timed_out) {
@@ -304,7 +332,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   jb += (unsigned)nplanes;
 }
 
-template <int SCHEME, bool WT, class G>
+template <int SCHEME, bool WT, class G, bool FULL>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_kernel(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
                      Layout L, Model<float> m, WtDesc wt, RecoverDesc rd, ZSched zs, unsigned* __restrict__ flags,
@@ -323,7 +351,7 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   __syncthreads();
   unsigned jb = 0;
   bool timed_out = false;
-  pair_unit<SCHEME, WT, G>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY,
+  pair_unit<SCHEME, WT, G, FULL>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY,
                            zs.z0(blockIdx.z), zs.len(blockIdx.z, L.nz), flags, smem, bars, jb, timed_out, wait_limit);
 }
 
@@ -388,15 +416,31 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
 
 template <int SCHEME, class G>
 cudaError_t set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(step_pair_kernel<SCHEME, true, G>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_pair_kernel<SCHEME, false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             G::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_pair_batch_kernel<SCHEME, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             G::SMEM);
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* fn) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  };
+  set((const void*)step_pair_kernel<SCHEME, true, G, false>);
+  set((const void*)step_pair_kernel<SCHEME, false, G, false>);
+  if (SCHEME == LBM_SCHEME_NND) {
+    set((const void*)step_pair_kernel<SCHEME, true, G, true>);
+    set((const void*)step_pair_kernel<SCHEME, false, G, true>);
+  }
+  set((const void*)step_pair_batch_kernel<SCHEME, G>);
   return e;
+}
+
+// The full-tile form (NND only): grids whose nx and ny are multiples of the tile.
+template <int SCHEME, bool WT, class G>
+void launch_full_or_not(dim3 grid, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
+                        const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
+                        unsigned* flags, unsigned wait_limit, cudaStream_t st) {
+  if (SCHEME == LBM_SCHEME_NND && L.nx % G::TX == 0 && L.ny % G::TY == 0)
+    step_pair_kernel<SCHEME, WT, G, SCHEME == LBM_SCHEME_NND><<<grid, G::THREADS, G::SMEM, st>>>(
+        map, fin, fout, L, m, wt, rd, zs, flags, wait_limit);
+  else
+    step_pair_kernel<SCHEME, WT, G, false><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs,
+                                                                               flags, wait_limit);
 }
 
 template <int SCHEME, class G>
@@ -406,11 +450,9 @@ cudaError_t launch_scheme(const CUtensorMap& map, const float* fin, float* fout,
   dim3 grid((L.nx + G::TX - 1) / G::TX, (L.ny + G::TY - 1) / G::TY, zs.nch);
   const bool any = wt.per[0] || wt.per[1] || wt.per[2] || wt.xlo || wt.xhi;
   if (any)
-    step_pair_kernel<SCHEME, true, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs, flags,
-                                                                         wait_limit);
+    launch_full_or_not<SCHEME, true, G>(grid, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
   else
-    step_pair_kernel<SCHEME, false, G><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs, flags,
-                                                                          wait_limit);
+    launch_full_or_not<SCHEME, false, G>(grid, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
   return cudaGetLastError();
 }
 

@@ -194,8 +194,9 @@ __device__ __forceinline__ void split_unit(const CUtensorMap* tin, const float* 
       const int i = FS::lo + j;
       const float2 Z1 = ld2(P1 + i * PL + c);
       Fn[j] = Z1;
+      float2 unused;
       out[j] = pm::field_update<SCHEME, BX>(m, i, P0 + i * PL + c, F[j], Z1, P2 + i * PL + c, h1[j], h2[j],
-                                            carry[j], pm::feq(m, r, i));
+                                            carry[j], unused, pm::feq(m, r, i));
     }
     const long long g = gbase + (long long)k * L.plane;
     if (act1) {

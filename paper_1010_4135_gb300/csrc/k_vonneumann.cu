@@ -178,8 +178,16 @@ __device__ double spectral_radius(const Mat& M) {
     M.at(k + 1, k) = (-alpha) * phase;
     for (int i = k + 2; i < n; ++i) M.at(i, k) = mk(0.0, 0.0);
   }
-  // shifted QR on the unreduced diagonal blocks, eigenvalues only
+  // shifted QR on the unreduced diagonal blocks, eigenvalues only.  A
+  // subdiagonal entry is negligible below ulp times its diagonal neighbours
+  // or ulp times the matrix norm: the iteration's backward error is of that
+  // size anyway, and without the norm floor a cluster of tiny eigenvalues
+  // (those of G for dt = tau are O(Courant number)) is never split off
   const double ulp = 2.220446049250313e-16;
+  double nrm = 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int c = r > 0 ? r - 1 : 0; c < n; ++c) nrm = fmax(nrm, cabs1(M.at(r, c)));
+  const double floor_small = ulp * nrm;
   double radius = 0.0;
   int hi = n - 1, its = 0, total = 0;
   double gc[VN];
@@ -188,7 +196,7 @@ __device__ double spectral_radius(const Mat& M) {
     int l = hi;
     while (l > 0) {
       const double tst = cabs1(M.at(l - 1, l - 1)) + cabs1(M.at(l, l));
-      if (cabs1(M.at(l, l - 1)) <= ulp * (tst > 0.0 ? tst : 1.0)) {
+      if (cabs1(M.at(l, l - 1)) <= fmax(ulp * tst, floor_small)) {
         M.at(l, l - 1) = mk(0.0, 0.0);
         break;
       }

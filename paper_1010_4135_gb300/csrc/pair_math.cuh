@@ -156,13 +156,35 @@ __device__ __forceinline__ float2 feq(const Model<float>& m, const Mom& r, int i
 // q: the pair in plane tile k (field i); Z1: the pair in plane k+1, Z2p: the
 // field's tile in plane k+2 at the pair; h1, h2: the pair in planes k-1, k-2
 // (registers); carry: the minmod of the lower z interface (NND), replaced by
-// that of the upper one.
-template <int SCHEME, int BX>
+// that of the upper one.  DZ (NND, diagonal velocities with v_z > 0): the
+// lower z difference f_k - f_{k-1} is carried in dz (the upper difference of
+// the plane before, the same rounded value) instead of being formed from H,
+// and dz takes this plane's upper difference.
+template <int SCHEME, int BX, bool DZ = false>
 __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, const float* q, float2 B, float2 Z1,
-                                               const float* Z2p, float2 H, float2 H2, float2& carry, float2 fe) {
+                                               const float* Z2p, float2 H, float2 H2, float2& carry, float2& dz,
+                                               float2 fe) {
   const float2 half = bc2(0.5f);
-  float2 conv = make_float2(0.f, 0.f);
-  float2 S = make_float2(0.f, 0.f);
+  // the convection and neighbour sums start from their first term (0 + x is
+  // not an identity for x = -0, so the compiler keeps an add with 0); conv
+  // holds the negated sum when its first term enters with a minus sign (cneg),
+  // folded into the coefficient at the end.  i is a compile-time constant, so
+  // the bookkeeping folds away.
+  float2 conv = make_float2(0.f, 0.f), S = make_float2(0.f, 0.f);
+  bool have_c = false, cneg = false, have_s = false;
+  auto acc = [&](float2 G, bool plus) {
+    if (!have_c) {
+      conv = G;
+      cneg = !plus;
+      have_c = true;
+    } else {
+      conv = (plus != cneg) ? add(conv, G) : sub(conv, G);
+    }
+  };
+  auto nsum = [&](float2 v) {
+    S = have_s ? add(S, v) : v;
+    have_s = true;
+  };
   // ---- x: neighbour pairs A = (x-2, x-1), C = (x+2, x+3)
   {
     const int sg = vsign(i, 0);
@@ -183,7 +205,7 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
         } else {
           G = make_float2(e1, e2);
         }
-        conv = add(conv, G);
+        acc(G, true);
       } else if (sg < 0) {
         const float e4 = C.y - C.x;
         float2 G;
@@ -199,9 +221,9 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
         } else {
           G = make_float2(e2, e3);
         }
-        conv = sub(conv, G);
+        acc(G, false);
       }
-      if (i <= 6) S = add(S, make_float2(A.y + B.y, B.x + C.x));
+      if (i <= 6) nsum(make_float2(A.y + B.y, B.x + C.x));
     }
   }
   // ---- y: rows y-2 .. y+2 of the same pair
@@ -220,7 +242,7 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
         } else {
           G = D0;
         }
-        conv = add(conv, G);
+        acc(G, true);
       } else if (sg < 0) {
         const float2 P2y = ld2(q + 2 * BX);
         const float2 D1 = sub(P1y, B);
@@ -232,27 +254,30 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
         } else {
           G = D1;
         }
-        conv = sub(conv, G);
+        acc(G, false);
       }
-      if (i <= 6) S = add(S, add(M1, P1y));
+      if (i <= 6) nsum(add(M1, P1y));
     }
   }
   // ---- z: planes z+1, z+2 from the ring, z-1 (z-2) from registers
   {
     const int sg = vsign(i, 2);
     if (sg > 0) {
-      const float2 D0 = sub(B, H);
+      constexpr bool kCarried = DZ && SCHEME == LBM_SCHEME_NND;
+      const float2 D0 = (kCarried && i >= 7) ? dz : sub(B, H);
       float2 G;
       if (SCHEME == LBM_SCHEME_NND) {
-        const float2 mA = mmc2(sub(Z1, B), D0);
+        const float2 Dup = sub(Z1, B);
+        const float2 mA = mmc2(Dup, D0);
         G = fma2(half, sub(mA, carry), D0);
         carry = mA;
+        if (kCarried && i >= 7) dz = Dup;
       } else if (SCHEME == LBM_SCHEME_UPWIND2) {
         G = mul(half, add(fma2(bc2(3.f), B, mul(bc2(-4.f), H)), H2));
       } else {
         G = D0;
       }
-      conv = add(conv, G);
+      acc(G, true);
     } else if (sg < 0) {
       const float2 Z2 = ld2(Z2p);
       const float2 D1 = sub(Z1, B);
@@ -266,15 +291,15 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
       } else {
         G = D1;
       }
-      conv = sub(conv, G);
+      acc(G, false);
     }
-    if (i <= 6) S = add(S, add(H, Z1));
+    if (i <= 6) nsum(add(H, Z1));
   }
   const float keep = i == 0 ? m.keep0 : (i <= 6 ? m.keep1 : m.keep2);
   const float kk = i == 0 ? 0.f : (i <= 6 ? m.k1 : m.k2);
   const float lam = i == 0 ? m.lam0 : (i <= 6 ? m.lam1 : 0.f);
   float2 o = fma2(bc2(m.dt_tau), fe, mul(bc2(keep), B));
-  if (i != 0) o = fma2(bc2(-kk), conv, o);
+  if (i != 0) o = fma2(bc2(cneg ? kk : -kk), conv, o);
   if (i <= 6) o = fma2(bc2(lam), S, o);
   return o;
 }

@@ -209,6 +209,22 @@ class Server:
         self.prep_s = collections.Counter()
         self._prep_lock = threading.Lock()
 
+    def _warm_workers(self, pool):
+        """Before the clock starts: every preparation thread sets up its CUDA
+        stream and runs the parameter service once, so that the first
+        requests do not pay that set-up in their latency."""
+        if not self.vn_device:
+            return
+        gate = threading.Barrier(self.prep_workers)
+
+        def warm():
+            gate.wait(timeout=120)
+            stability.max_growth_device([(1.0, 0.0, 0.0, 0.0, 1.0)], [(2.0, 6.0, 4.0, 1.4, 1e-5, 1e-5, 0.01)],
+                                        nk=2, stream=_service_stream())
+
+        for f in [pool.submit(warm) for _ in range(self.prep_workers)]:
+            f.result()
+
     def _note_prep(self, params_s, fields_s):
         with self._prep_lock:
             self.prep_s["params"] += params_s
@@ -275,6 +291,7 @@ class Server:
         ticks: collections.deque = collections.deque()  # events of launched ticks
         used = 0
         pool = cf.ThreadPoolExecutor(max_workers=self.prep_workers)
+        self._warm_workers(pool)
         t0 = time.perf_counter()
 
         def clock():

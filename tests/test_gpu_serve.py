@@ -16,9 +16,9 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _trace():
+def _trace(steps=(20, 70)):
     grids = ((16, 16, 16), (24, 16, 16), (20, 12, 12), (32, 16, 8))
-    tr = workloads.serving_trace(seed=7, n=8, rate=200.0, grids=grids, steps=(20, 70))
+    tr = workloads.serving_trace(seed=7, n=8, rate=200.0, grids=grids, steps=steps)
     return tr
 
 
@@ -26,10 +26,12 @@ def _trace():
 def test_served_results_equal_alone_and_budget_is_respected(policy):
     from paper_1010_4135_gb300 import serve
     from paper_1010_4135_gb300 import sim as S
-    tr = _trace()
+    # all eight arrive within 40 ms and are prepared together (one worker
+    # each), and each runs long enough that the next ones are ready before it ends
+    tr = _trace(steps=(300, 600))
     sizes = [serve.workspace_bytes(r["grid"]) for r in tr]
     budget = 2 * max(sizes) + min(sizes)  # forces waiting for memory to free up
-    srv = serve.Server(hbm_budget=budget, max_batch=3, tick=16, keep_results=True, policy=policy)
+    srv = serve.Server(hbm_budget=budget, max_batch=3, tick=16, keep_results=True, policy=policy, prep_workers=8)
     done = srv.run(tr)
     assert len(done) == len(tr)
     assert srv.peak_bytes <= budget and srv.peak_batch <= 3
