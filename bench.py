@@ -227,7 +227,7 @@ def measured_peak():
 # sources of each profiled kernel: its recorded DRAM traffic is used only while
 # these files are unchanged
 KERNEL_SOURCES = {
-    "step_fp32": ("k_pair.cu", "tma_ring.cuh", "lbm_internal.cuh"),
+    "step_fp32": ("k_pair.cu", "pair_math.cuh", "tma_ring.cuh", "lbm_internal.cuh"),
     "step_fp64": ("k_plain.cu", "lbm_internal.cuh"),
 }
 

@@ -70,7 +70,7 @@ struct PairGeo {
 };
 // 32 x 8 tiles (the single-cell tiled kernel's box, 40 x 12): two CTAs of 4
 // warps per SM, L2 prefetch two planes ahead (256^3: 0.475 ms per step, 0.488
-// without the prefetch).
+// without the prefetch; one or three planes ahead: no faster).
 using Geo32 = PairGeo<ring::TX, ring::TY, 2>;
 // 64 x 8 tiles (box 72 x 12 x 1 x 15): one CTA of 8 warps per SM, 288-byte
 // row reads, run as two split halves.  Its data movement alone (ring +
@@ -104,7 +104,7 @@ __device__ __forceinline__ bool half_sync_or(unsigned id, bool v) {
 // threads of the CTA call it together; timed_out is uniform.  FULL: every
 // tile lies inside the grid (nx and ny multiples of the tile), so every pair
 // is active and the activity tests fold away.
-template <int SCHEME, bool WT, class G, bool FULL = false>
+template <int SCHEME, bool WT, class G, bool FULL = false, bool R1 = false>
 __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* __restrict__ fin,
                                           float* __restrict__ fout, const Layout& L, const Model<float>& m,
                                           const WtDesc& wt, const RecoverDesc& rd, int x0, int y0, int z0,
@@ -219,7 +219,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     float2 out[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
-      out[i] = pm::field_update<SCHEME, BX, DZ>(m, i, P0 + i * PL + c, F[i], ld2(P1 + i * PL + c), P2 + i * PL + c,
+      out[i] = pm::field_update<SCHEME, BX, DZ, R1>(m, i, P0 + i * PL + c, F[i], ld2(P1 + i * PL + c), P2 + i * PL + c,
                                                 h1[i], h2[i], carry[i], dz[i], pm::feq(m, r, i));
     const long long g = gbase + (long long)k * L.plane;
     if (act1) {
@@ -332,7 +332,8 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
   jb += (unsigned)nplanes;
 }
 
-template <int SCHEME, bool WT, class G, bool FULL>
+// FULL: full tiles; R1: dt = tau (dt/tau = 1, keep_2 = 0), used with FULL only
+template <int SCHEME, bool WT, class G, bool FULL, bool R1 = false>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_kernel(const __grid_constant__ CUtensorMap tin, const float* __restrict__ fin, float* __restrict__ fout,
                      Layout L, Model<float> m, WtDesc wt, RecoverDesc rd, ZSched zs, unsigned* __restrict__ flags,
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
   __syncthreads();
   unsigned jb = 0;
   bool timed_out = false;
-  pair_unit<SCHEME, WT, G, FULL>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY,
+  pair_unit<SCHEME, WT, G, FULL, R1>(&tin, fin, fout, L, m, wt, rd, blockIdx.x * G::TX, blockIdx.y * G::TY,
                            zs.z0(blockIdx.z), zs.len(blockIdx.z, L.nz), flags, smem, bars, jb, timed_out, wait_limit);
 }
 
@@ -425,6 +426,8 @@ cudaError_t set_attributes() {
   if (SCHEME == LBM_SCHEME_NND) {
     set((const void*)step_pair_kernel<SCHEME, true, G, true>);
     set((const void*)step_pair_kernel<SCHEME, false, G, true>);
+    set((const void*)step_pair_kernel<SCHEME, true, G, true, true>);
+    set((const void*)step_pair_kernel<SCHEME, false, G, true, true>);
   }
   set((const void*)step_pair_batch_kernel<SCHEME, G>);
   return e;
@@ -435,9 +438,13 @@ template <int SCHEME, bool WT, class G>
 void launch_full_or_not(dim3 grid, const CUtensorMap& map, const float* fin, float* fout, const Layout& L,
                         const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
                         unsigned* flags, unsigned wait_limit, cudaStream_t st) {
-  if (SCHEME == LBM_SCHEME_NND && L.nx % G::TX == 0 && L.ny % G::TY == 0)
-    step_pair_kernel<SCHEME, WT, G, SCHEME == LBM_SCHEME_NND><<<grid, G::THREADS, G::SMEM, st>>>(
-        map, fin, fout, L, m, wt, rd, zs, flags, wait_limit);
+  constexpr bool NND = SCHEME == LBM_SCHEME_NND;
+  if (NND && L.nx % G::TX == 0 && L.ny % G::TY == 0 && m.dt_tau == 1.0f && m.keep2 == 0.0f)
+    step_pair_kernel<SCHEME, WT, G, NND, NND><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs,
+                                                                                  flags, wait_limit);
+  else if (NND && L.nx % G::TX == 0 && L.ny % G::TY == 0)
+    step_pair_kernel<SCHEME, WT, G, NND><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs, flags,
+                                                                             wait_limit);
   else
     step_pair_kernel<SCHEME, WT, G, false><<<grid, G::THREADS, G::SMEM, st>>>(map, fin, fout, L, m, wt, rd, zs,
                                                                                flags, wait_limit);

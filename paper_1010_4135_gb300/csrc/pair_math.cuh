@@ -123,29 +123,42 @@ __device__ __forceinline__ unsigned health(const Mom& r, bool act0, bool act1) {
   return bad;
 }
 
-// f^eq_i of the pair (Eq. "eq"), per shell A + B w + D w^2 with the linear
-// term fused: (A + D w^2) + B w is one fma, not a product and a sum (the
-// compiler may fuse a packed product into a later sum in one kernel and not
-// in another; written as an fma, every kernel rounds it the same way).  i is
-// a compile-time constant after unrolling.
+// f^eq_i of the pair (Eq. "eq"): rho (A + B w + D w^2) per shell, evaluated
+// as (rho A + rho D w^2) + rho B w with rho folded into the shell's three
+// coefficients once per pair (Shell below) and the linear term fused: one fma
+// each, not a product and a sum (the compiler may fuse a packed product into
+// a later sum in one kernel and not in another; written as fmas, every
+// kernel rounds them the same way).  i is a compile-time constant after
+// unrolling.
+struct Shell {
+  float2 rA, rB, rD;  // rho A, rho B, rho D
+};
+__device__ __forceinline__ Shell axis_shell(const Model<float>& m, const Mom& r) {
+  const float2 A = fma2(bc2(m.AaT), r.T, fma2(bc2(m.AaU), r.usq, bc2(m.Aa0)));
+  const float2 B = fma2(bc2(m.BaT), r.T, fma2(bc2(m.BaU), r.usq, bc2(m.Ba0)));
+  return {mul(r.rho, A), mul(r.rho, B), mul(r.rho, bc2(m.Da))};
+}
+__device__ __forceinline__ Shell diag_shell(const Model<float>& m, const Mom& r) {
+  const float2 A = fma2(bc2(m.AdT), r.T, fma2(bc2(m.AdU), r.usq, bc2(m.Ad0)));
+  const float2 B = fma2(bc2(m.BdT), r.T, fma2(bc2(m.BdU), r.usq, bc2(m.Bd0)));
+  return {mul(r.rho, A), mul(r.rho, B), mul(r.rho, bc2(m.Dd))};
+}
 __device__ __forceinline__ float2 feq(const Model<float>& m, const Mom& r, int i) {
   if (i == 0) return mul(r.rho, mul(bc2(m.AR), r.T));
   if (i <= 6) {
-    const float2 Aa = fma2(bc2(m.AaT), r.T, fma2(bc2(m.AaU), r.usq, bc2(m.Aa0)));
-    const float2 Ba = fma2(bc2(m.BaT), r.T, fma2(bc2(m.BaU), r.usq, bc2(m.Ba0)));
+    const Shell sh = axis_shell(m, r);
     const int a = (i - 1) / 2;
     const float2 w = mul(bc2(m.c1), a == 0 ? r.ux : (a == 1 ? r.uy : r.uz));
-    const float2 q = fma2(bc2(m.Da), mul(w, w), Aa);
-    return mul(r.rho, fma2((i - 1) % 2 == 0 ? Ba : neg(Ba), w, q));
+    const float2 q = fma2(sh.rD, mul(w, w), sh.rA);
+    return fma2((i - 1) % 2 == 0 ? sh.rB : neg(sh.rB), w, q);
   }
-  const float2 Ad = fma2(bc2(m.AdT), r.T, fma2(bc2(m.AdU), r.usq, bc2(m.Ad0)));
-  const float2 Bd = fma2(bc2(m.BdT), r.T, fma2(bc2(m.BdU), r.usq, bc2(m.Bd0)));
+  const Shell sh = diag_shell(m, r);
   // k = 0..3 are (+ + +), (+ + -), (+ - +), (+ - -); fields 7+k and 14-k are opposite
   const int k = i <= 10 ? i - 7 : 14 - i;
   const float2 sxy = add(r.ux, r.uy), dxy = sub(r.ux, r.uy);
   const float2 w = mul(bc2(m.s), k == 0 ? add(sxy, r.uz) : (k == 1 ? sub(sxy, r.uz) : (k == 2 ? add(dxy, r.uz) : sub(dxy, r.uz))));
-  const float2 q = fma2(bc2(m.Dd), mul(w, w), Ad);
-  return mul(r.rho, fma2(i <= 10 ? Bd : neg(Bd), w, q));
+  const float2 q = fma2(sh.rD, mul(w, w), sh.rA);
+  return fma2(i <= 10 ? sh.rB : neg(sh.rB), w, q);
 }
 
 // New value of field i of the pair (i a compile-time constant after
@@ -160,7 +173,7 @@ __device__ __forceinline__ float2 feq(const Model<float>& m, const Mom& r, int i
 // lower z difference f_k - f_{k-1} is carried in dz (the upper difference of
 // the plane before, the same rounded value) instead of being formed from H,
 // and dz takes this plane's upper difference.
-template <int SCHEME, int BX, bool DZ = false>
+template <int SCHEME, int BX, bool DZ = false, bool R1 = false>
 __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, const float* q, float2 B, float2 Z1,
                                                const float* Z2p, float2 H, float2 H2, float2& carry, float2& dz,
                                                float2 fe) {
@@ -298,7 +311,12 @@ __device__ __forceinline__ float2 field_update(const Model<float>& m, int i, con
   const float keep = i == 0 ? m.keep0 : (i <= 6 ? m.keep1 : m.keep2);
   const float kk = i == 0 ? 0.f : (i <= 6 ? m.k1 : m.k2);
   const float lam = i == 0 ? m.lam0 : (i <= 6 ? m.lam1 : 0.f);
-  float2 o = fma2(bc2(m.dt_tau), fe, mul(bc2(keep), B));
+  // keep_i f + (dt/tau) f^eq.  R1 (dt = tau): dt/tau = 1, so the product with
+  // it is f^eq exactly, and keep_2 = 1 - dt/tau = 0 for the diagonal
+  // velocities, whose sum is then f^eq exactly: bitwise the general form
+  float2 o;
+  if (R1) o = i >= 7 ? fe : fma2(bc2(keep), B, fe);
+  else o = fma2(bc2(keep), B, mul(bc2(m.dt_tau), fe));
   if (i != 0) o = fma2(bc2(cneg ? kk : -kk), conv, o);
   if (i <= 6) o = fma2(bc2(lam), S, o);
   return o;
