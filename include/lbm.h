@@ -131,7 +131,8 @@ LBM_API size_t lbm_workspace_bytes(const lbm_grid* grid, int32_t precision);
  * aligned; cuda_stream is a cudaStream_t (NULL = legacy default stream).
  * The f state is undefined until lbm_init or lbm_set_f.  Errors: LBM_EINVAL
  * (sizes < 1, c1 == c2, eta0 <= 0, tau/dt/dx <= 0, gamma <= 1, unpaired
- * periodic faces, EXTRAPOLATE with fewer than 2 cells, NULL pointers),
+ * periodic faces, EXTRAPOLATE with fewer than 2 cells, a padded field of
+ * 2^32 or more cells, NULL pointers),
  * LBM_ENOMEM (workspace too small), LBM_ECUDA. */
 LBM_API int lbm_create(const lbm_grid* grid, const lbm_vset* vset, double tau, double dt, double dx,
                int32_t precision, void* d_workspace, size_t ws_bytes, void* cuda_stream, lbm_sim** out);
@@ -255,6 +256,18 @@ LBM_API int lbm_set_halo(lbm_sim* sim, int32_t side, const void* buf, int32_t on
 LBM_API int lbm_vn_max_growth(const double* states, int32_t nstates, const double* params, int32_t nparams,
                               const double* dirs, int32_t ndirs, int32_t nk, int32_t dissipation, double* out,
                               void* cuda_stream);
+
+/* Diagnostic: y[j] = 1/x[j] for n floats as the FP32 step kernels form the
+ * inverse density (the hardware approximation rcp.approx.ftz.f32 refined by
+ * one Newton-Raphson step): |y x - 1| <= 2^-24 + 2^-40 for 2^-100 <= |x| <=
+ * 2^100 and <= 2^-23 for 2^-125 <= |x| <= 2^125 (beyond 2^100 the Newton
+ * correction is subnormal), not always the nearest float, never more than
+ * one float from it; NaN for x = 0, +-inf, NaN and
+ * subnormal x (flushed to zero), 0 for |x| >= 2^127 (a subnormal 1/x is
+ * flushed to zero).  d_x, d_y: device arrays
+ * (they may be the same array); asynchronous on cuda_stream.  Errors:
+ * LBM_EINVAL (n < 0, NULL pointers with n > 0), LBM_ECUDA. */
+LBM_API int lbm_reciprocal_fp32(const float* d_x, float* d_y, int64_t n, void* cuda_stream);
 
 /* Synchronise and read the health flag bits (LBM_HEALTH_*) accumulated since
  * lbm_init; returns LBM_ETIMEOUT when a bounded device wait ran out

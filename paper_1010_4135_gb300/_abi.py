@@ -67,6 +67,7 @@ SIGNATURES = [
     ("lbm_set_halo", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32]),
     ("lbm_vn_max_growth", ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+    ("lbm_reciprocal_fp32", ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
     ("lbm_health", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
     ("lbm_sync", ctypes.c_int, [_vp]),
     ("lbm_steps_done", ctypes.c_int64, [_vp]),
@@ -138,6 +139,7 @@ lbm_conserved_noalloc = _forward("lbm_conserved_noalloc")
 lbm_get_halo_source = _forward("lbm_get_halo_source")
 lbm_set_halo = _forward("lbm_set_halo")
 lbm_vn_max_growth = _forward("lbm_vn_max_growth")
+lbm_reciprocal_fp32 = _forward("lbm_reciprocal_fp32")
 lbm_health = _forward("lbm_health")
 lbm_sync = _forward("lbm_sync")
 lbm_steps_done = _forward("lbm_steps_done")

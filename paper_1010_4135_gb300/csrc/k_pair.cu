@@ -191,9 +191,10 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     for (int i = 7; i < NV; ++i)
       if (vsign(i, 2) > 0) dz[i] = pm::sub(ld2(Q0 + i * PL + c), h1[i]);
   }
-  // health: running minima of rho and T and a running sum of the macroscopic
-  // values of each cell of the pair (a non-finite value makes the sum
-  // non-finite), judged once at the end of the unit
+  // health: running minima of rho and T and a running sum of rho + T of each
+  // cell of the pair, judged once at the end of the unit.  A non-finite rho or
+  // T makes the sum non-finite, and so does a non-finite velocity: T is
+  // (E/rho - u^2)/b, -inf or NaN when u^2 is inf or NaN.
   float2 hmin_rho = make_float2(INFINITY, INFINITY), hmin_T = hmin_rho, hsum = make_float2(0.f, 0.f);
   // write-through targets that do not depend on the plane: the periodic y and
   // x images of this pair (element offsets from its own index, 0 = none)
@@ -215,13 +216,15 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
     const pm::Mom r = pm::moments(m, rd, F, P0, c, PL, act0, act1);
     hmin_rho = make_float2(fminf(hmin_rho.x, r.rho.x), fminf(hmin_rho.y, r.rho.y));
     hmin_T = make_float2(fminf(hmin_T.x, r.T.x), fminf(hmin_T.y, r.T.y));
-    hsum = pm::add(hsum, pm::add(pm::add(r.rho, r.T), pm::add(pm::add(r.ux, r.uy), r.uz)));
+    hsum = pm::add(hsum, pm::add(r.rho, r.T));
     float2 out[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       out[i] = pm::field_update<SCHEME, BX, DZ, R1>(m, i, P0 + i * PL + c, F[i], ld2(P1 + i * PL + c), P2 + i * PL + c,
                                                 h1[i], h2[i], carry[i], dz[i], pm::feq(m, r, i));
-    const long long g = gbase + (long long)k * L.plane;
+    // the pair's element offset within a field: below 2^32 (the host rejects
+    // longer fields), so the fields' stores share one 32-bit offset
+    const unsigned g = (unsigned)gbase + (unsigned)k * (unsigned)L.plane;
     if (act1) {
 #pragma unroll
       for (int i = 0; i < NV; ++i) *reinterpret_cast<float2*>(fout + i * L.fs + g) = out[i];
@@ -240,7 +243,7 @@ __device__ __forceinline__ void pair_unit(const CUtensorMap* tin, const float* _
         for (int q = 0; q < 3; ++q) {
           const long long off = q == 0 ? img_y : (q == 1 ? img_z : img_x);
           if (off == 0) continue;
-          const long long at = g + off;
+          const long long at = (long long)g + off;
           if (act1) {
 #pragma unroll
             for (int i = 0; i < NV; ++i) *reinterpret_cast<float2*>(fout + i * L.fs + at) = out[i];
@@ -519,6 +522,27 @@ cudaError_t launch_step_pair(int cols, int scheme, const CUtensorMap& map, const
                              const ZSched& zs, unsigned* flags, unsigned wait_limit, cudaStream_t st) {
   if (cols == 64) return launch_geo<Geo64>(scheme, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
   return launch_geo<Geo32>(scheme, map, fin, fout, L, m, wt, rd, zs, flags, wait_limit, st);
+}
+
+// 1/x as the FP32 step kernels form the inverse density (pm::rcp2), two
+// values per thread; an odd tail pads its second lane with 1.
+__global__ void __launch_bounds__(256) reciprocal_kernel(const float* __restrict__ x, float* __restrict__ y,
+                                                         long long n) {
+  const long long stride = 2LL * gridDim.x * blockDim.x;
+  for (long long i = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x); i < n; i += stride) {
+    const bool two = i + 1 < n;
+    const float2 r = pm::rcp2(make_float2(x[i], two ? x[i + 1] : 1.f));
+    y[i] = r.x;
+    if (two) y[i + 1] = r.y;
+  }
+}
+
+cudaError_t launch_reciprocal_fp32(const float* x, float* y, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long pairs = (n + 1) / 2;
+  const int blocks = (int)std::min<long long>((pairs + 255) / 256, 152LL * 8);
+  reciprocal_kernel<<<blocks, 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
 }
 
 }  // namespace lbm

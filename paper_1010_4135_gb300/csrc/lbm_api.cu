@@ -45,7 +45,12 @@ bool grid_ok(const lbm_grid* g) {
     }
     if ((g->bc_lo[a] == LBM_BC_PERIODIC) != (g->bc_hi[a] == LBM_BC_PERIODIC)) return false;
   }
-  return true;
+  // one padded field must hold fewer than 2^32 elements (the tiled kernels
+  // index within a field in 32 bits); two FP32 states of that size would
+  // already take more than 500 GB
+  const size_t sx = align_up((size_t)lbm::OX + (size_t)g->nx + 2, 32);
+  const size_t fs = align_up(sx * (size_t)(g->ny + 4) * (size_t)(g->nz + 4), 64);
+  return fs <= 0xffffffffull;
 }
 
 Layout make_layout(const lbm_grid* g) {
@@ -1058,4 +1063,10 @@ extern "C" int lbm_vn_max_growth(const double* states, int32_t nstates, const do
                                    (cudaStream_t)cuda_stream) == cudaSuccess
              ? LBM_OK
              : LBM_ECUDA;
+}
+
+extern "C" int lbm_reciprocal_fp32(const float* x, float* y, int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return LBM_EINVAL;
+  return lbm::launch_reciprocal_fp32(x, y, (long long)n, (cudaStream_t)cuda_stream) == cudaSuccess ? LBM_OK
+                                                                                                    : LBM_ECUDA;
 }

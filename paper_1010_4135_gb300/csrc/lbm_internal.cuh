@@ -304,6 +304,7 @@ cudaError_t launch_step_split_batch(int scheme, const BatchTable& tab, int grid,
 // Von Neumann service: out[p] = max |omega| of G(k) (Sec. 3) over the states
 // (rho, u1, u2, u3, T), directions and nk wave numbers, for each parameter
 // set p = (c1, c2, eta0, gamma, dt, tau, dx); device pointers; out zeroed here.
+cudaError_t launch_reciprocal_fp32(const float* x, float* y, long long n, cudaStream_t st);
 cudaError_t launch_vn_max_growth(const double* states, int nstates, const double* params, int nparams,
                                  const double* dirs, int ndirs, int nk, int dissipation, double* out,
                                  cudaStream_t st);

@@ -30,6 +30,25 @@ __device__ __forceinline__ float2 mmc2(float2 x, float2 d) {
   return make_float2(mmc(x.x, fminf(d.x, 0.f), fmaxf(d.x, 0.f)), mmc(x.y, fminf(d.y, 0.f), fmaxf(d.y, 0.f)));
 }
 
+// 1/a for both cells: the hardware approximation r0 (PTX rcp.approx.ftz.f32,
+// relative error d of a few 2^-23 at most) refined by one Newton-Raphson
+// step for the reciprocal, r = r0 - r0 (a r0 - 1) (the iteration
+// x <- x (2 - a x) of Newton-Raphson division, written with the residual
+// formed by one fma).  With r0 = (1 + d)/a the residual a r0 - 1 = d is exact
+// in the fma, and r = (1 - d^2)/a up to the final rounding: |r a - 1| <=
+// 2^-24 + d^2 + O(2^-46) while the correction r0 (a r0 - 1) stays normal
+// (|a| <= 2^100): the accuracy of one rounding, though not always the nearest
+// float.  a = 0 or +-inf (and subnormal a, flushed to 0) give NaN; a
+// cell with such a density fails the health checks.  Four packed operations
+// and two MUFU against two correctly rounded reciprocals.
+__device__ __forceinline__ float2 rcp2(float2 a) {
+  float2 r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0.x) : "f"(a.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0.y) : "f"(a.y));
+  const float2 res = fma2(a, r0, bc2(-1.f));
+  return sub(r0, mul(res, r0));
+}
+
 // Macroscopic state of a pair.
 struct Mom {
   float2 rho, ux, uy, uz, T, usq;
@@ -75,7 +94,7 @@ __device__ __forceinline__ Mom moments(const Model<float>& m, const RecoverDesc&
                          mul(bc2(m.s), sub(add(add(F[7], F[9]), add(F[11], F[13])),
                                            add(add(F[8], F[10]), add(F[12], F[14])))));
   const float2 E = fma2(bc2(m.eta0sq), F[0], fma2(bc2(m.c1sq), sa, mul(bc2(m.c2sq), sd)));
-  const float2 ir = make_float2(__frcp_rn(r.rho.x), __frcp_rn(r.rho.y));
+  const float2 ir = rcp2(r.rho);
   r.ux = mul(mx, ir);
   r.uy = mul(my, ir);
   r.uz = mul(mz, ir);

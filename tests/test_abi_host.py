@@ -45,6 +45,12 @@ def _grid(A, nx=10, ny=4, nz=3, lo=(0, 0, 0), hi=(0, 0, 0)):
     return A.make_grid(nx, ny, nz, lo, hi)
 
 
+def test_largest_field_below_2_32_cells_is_accepted(A):
+    # rows of 2038 cells pad to 2048 (8 + 2038 + 2), 2044 rows to 2048, 1020 planes to 1024:
+    # 2^32 cells, the first field refused; 1019 planes (1023 padded) fit
+    assert A.lbm_workspace_bytes(ctypes.byref(_grid(A, 2038, 2044, 1019)), A.LBM_FP32) > 0
+
+
 def test_workspace_bytes(A):
     small = A.lbm_workspace_bytes(ctypes.byref(_grid(A, 10, 4, 3)), A.LBM_FP64)
     big = A.lbm_workspace_bytes(ctypes.byref(_grid(A, 64, 64, 64)), A.LBM_FP64)
@@ -60,6 +66,8 @@ def test_workspace_bytes(A):
 @pytest.mark.parametrize("kw", [
     dict(nx=0), dict(ny=-1), dict(lo=(0, 0, 0), hi=(1, 0, 0)), dict(lo=(9, 0, 0), hi=(9, 0, 0)),
     dict(nx=1, lo=(2, 0, 0), hi=(2, 0, 0)),
+    # a padded field of 2^32 or more cells (the tiled kernels index a field in 32 bits)
+    dict(nx=2038, ny=2044, nz=1020),
 ])
 def test_invalid_grids_have_no_workspace(A, kw):
     args = dict(nx=10, ny=4, nz=3, lo=(0, 0, 0), hi=(0, 0, 0))
