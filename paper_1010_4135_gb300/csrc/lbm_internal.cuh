@@ -184,6 +184,20 @@ __device__ __forceinline__ R clamp_mm(R x, R lo, R hi) {
   return fmin(fmax(x, lo), hi);
 }
 
+// minmod(x, d) of two doubles from their bit patterns, on the integer pipes:
+// 0 when the signs differ, else the operand of smaller magnitude (magnitudes
+// of IEEE doubles order like their bit patterns without the sign).  The same
+// value as the clamp form for finite operands (a zero result may differ in
+// sign).  GB300 executes FP64 at a small fraction of its FP32 rate and a
+// double min or max is an FP64 comparison, so the FP64 step kernel, bound by
+// its FP64 pipe, takes its minmods here.
+__device__ __forceinline__ double minmod_bits(double x, double d) {
+  const long long bx = __double_as_longlong(x), bd = __double_as_longlong(d);
+  constexpr long long kMag = 0x7fffffffffffffffLL;
+  const long long r = (bx & kMag) <= (bd & kMag) ? bx : bd;
+  return (bx ^ bd) < 0 ? 0.0 : __longlong_as_double(r);
+}
+
 // dx * d(v f)/dx / v along one axis, from the upwind-side stencil:
 // v > 0 uses f at I-2..I+1 (m2, m1, c, p1); v < 0 uses I-1..I+2 (m1, c, p1, p2).
 // NND: (h_{I+1/2} - h_{I-1/2}) / v with the limited fluxes of Sec. 3; both
@@ -193,6 +207,7 @@ __device__ __forceinline__ R grad_pos(R m2, R m1, R c, R p1) {
   if (SCHEME == LBM_SCHEME_UPWIND1) return c - m1;
   if (SCHEME == LBM_SCHEME_UPWIND2) return R(0.5) * ((R(3) * c - R(4) * m1) + m2);
   const R d0 = c - m1;
+  if constexpr (sizeof(R) == 8) return d0 + R(0.5) * (minmod_bits(p1 - c, d0) - minmod_bits(m1 - m2, d0));
   const R lo = fmin(d0, R(0)), hi = fmax(d0, R(0));
   return d0 + R(0.5) * (clamp_mm(p1 - c, lo, hi) - clamp_mm(m1 - m2, lo, hi));
 }
@@ -201,6 +216,7 @@ __device__ __forceinline__ R grad_neg(R m1, R c, R p1, R p2) {
   if (SCHEME == LBM_SCHEME_UPWIND1) return p1 - c;
   if (SCHEME == LBM_SCHEME_UPWIND2) return R(0.5) * ((R(4) * p1 - R(3) * c) - p2);
   const R d1 = p1 - c;
+  if constexpr (sizeof(R) == 8) return d1 - R(0.5) * (minmod_bits(p2 - p1, d1) - minmod_bits(c - m1, d1));
   const R lo = fmin(d1, R(0)), hi = fmax(d1, R(0));
   return d1 - R(0.5) * (clamp_mm(p2 - p1, lo, hi) - clamp_mm(c - m1, lo, hi));
 }
