@@ -365,7 +365,8 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
 // increment per unit, so fast and slow CTAs balance.  Every CTA overshoots
 // the queue once; the last CTA to finish resets the queue for the next
 // launch (stream order), which keeps the launch replayable in a CUDA graph.
-template <int SCHEME, class G>
+// FULL / R1: every grid of the table has full tiles / dt = tau (NND only).
+template <int SCHEME, class G, bool FULL = false, bool R1 = false>
 __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     step_pair_batch_kernel(const __grid_constant__ BatchTable tab) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -404,9 +405,9 @@ __global__ void __launch_bounds__(G::THREADS, G::CTAS_PER_SM)
     const WtDesc wt = it.wt;
     const RecoverDesc rd = it.rd;
     const ZSched zs = it.zs;
-    pair_unit<SCHEME, true, G>(&tab.map[e], it.fin, it.fout, L, m, wt, rd, (t % it.tiles_x) * G::TX,
-                               (t / it.tiles_x) * G::TY, zs.z0(chunk), zs.len(chunk, L.nz), it.flags, smem, bars,
-                               jb, timed_out, tab.wait_limit);
+    pair_unit<SCHEME, true, G, FULL, R1>(&tab.map[e], it.fin, it.fout, L, m, wt, rd, (t % it.tiles_x) * G::TX,
+                                         (t / it.tiles_x) * G::TY, zs.z0(chunk), zs.len(chunk, L.nz), it.flags, smem,
+                                         bars, jb, timed_out, tab.wait_limit);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -433,6 +434,10 @@ cudaError_t set_attributes() {
     set((const void*)step_pair_kernel<SCHEME, false, G, true, true>);
   }
   set((const void*)step_pair_batch_kernel<SCHEME, G>);
+  if (SCHEME == LBM_SCHEME_NND) {
+    set((const void*)step_pair_batch_kernel<SCHEME, G, true>);
+    set((const void*)step_pair_batch_kernel<SCHEME, G, true, true>);
+  }
   return e;
 }
 
@@ -502,8 +507,19 @@ PairShape pair_shape(int cols) {
 
 template <class G>
 void launch_batch_geo(int scheme, const BatchTable& tab, int grid, cudaStream_t st) {
+  // the full-tile and dt = tau forms when every grid of the table qualifies
+  bool full = true, r1 = true;
+  for (int e = 0; e < tab.n; ++e) {
+    const BatchItem& it = tab.item[e];
+    full = full && it.L.nx % G::TX == 0 && it.L.ny % G::TY == 0;
+    r1 = r1 && it.m.dt_tau == 1.0f && it.m.keep2 == 0.0f;
+  }
   switch (scheme) {
-    case LBM_SCHEME_NND: step_pair_batch_kernel<LBM_SCHEME_NND, G><<<grid, G::THREADS, G::SMEM, st>>>(tab); break;
+    case LBM_SCHEME_NND:
+      if (full && r1) step_pair_batch_kernel<LBM_SCHEME_NND, G, true, true><<<grid, G::THREADS, G::SMEM, st>>>(tab);
+      else if (full) step_pair_batch_kernel<LBM_SCHEME_NND, G, true><<<grid, G::THREADS, G::SMEM, st>>>(tab);
+      else step_pair_batch_kernel<LBM_SCHEME_NND, G><<<grid, G::THREADS, G::SMEM, st>>>(tab);
+      break;
     case LBM_SCHEME_UPWIND2:
       step_pair_batch_kernel<LBM_SCHEME_UPWIND2, G><<<grid, G::THREADS, G::SMEM, st>>>(tab);
       break;

@@ -317,10 +317,11 @@ cudaError_t launch_step_split(int scheme, const CUtensorMap& map, const float* f
                               const Model<float>& m, const WtDesc& wt, const RecoverDesc& rd, const ZSched& zs,
                               unsigned* flags, unsigned wait_limit, cudaStream_t st);
 cudaError_t launch_step_split_batch(int scheme, const BatchTable& tab, int grid, cudaStream_t st);
+// y = 1/x as the FP32 step kernels form the inverse density (device arrays).
+cudaError_t launch_reciprocal_fp32(const float* x, float* y, long long n, cudaStream_t st);
 // Von Neumann service: out[p] = max |omega| of G(k) (Sec. 3) over the states
 // (rho, u1, u2, u3, T), directions and nk wave numbers, for each parameter
 // set p = (c1, c2, eta0, gamma, dt, tau, dx); device pointers; out zeroed here.
-cudaError_t launch_reciprocal_fp32(const float* x, float* y, long long n, cudaStream_t st);
 cudaError_t launch_vn_max_growth(const double* states, int nstates, const double* params, int nparams,
                                  const double* dirs, int ndirs, int nk, int dissipation, double* out,
                                  cudaStream_t st);
