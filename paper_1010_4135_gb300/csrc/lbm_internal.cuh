@@ -186,16 +186,22 @@ __device__ __forceinline__ R clamp_mm(R x, R lo, R hi) {
 
 // minmod(x, d) of two doubles from their bit patterns, on the integer pipes:
 // 0 when the signs differ, else the operand of smaller magnitude (magnitudes
-// of IEEE doubles order like their bit patterns without the sign).  The same
-// value as the clamp form for finite operands (a zero result may differ in
-// sign).  GB300 executes FP64 at a small fraction of its FP32 rate and a
-// double min or max is an FP64 comparison, so the FP64 step kernel, bound by
-// its FP64 pipe, takes its minmods here.
+// of IEEE doubles order like their bit patterns without the sign, compared
+// here as (high word, low word)).  The same value as the clamp form for
+// finite operands (a zero result may differ in sign).  GB300 executes FP64 at
+// a small fraction of its FP32 rate and a double min or max is an FP64
+// comparison, so the FP64 step kernel, bound by its FP64 pipe, takes its
+// minmods here.  Written on 32-bit halves: the same selection on 64-bit
+// integers cost the FP64 pipe 3 more instructions per gradient.
 __device__ __forceinline__ double minmod_bits(double x, double d) {
-  const long long bx = __double_as_longlong(x), bd = __double_as_longlong(d);
-  constexpr long long kMag = 0x7fffffffffffffffLL;
-  const long long r = (bx & kMag) <= (bd & kMag) ? bx : bd;
-  return (bx ^ bd) < 0 ? 0.0 : __longlong_as_double(r);
+  const int hx = __double2hiint(x), hd = __double2hiint(d);
+  const unsigned lx = (unsigned)__double2loint(x), ld = (unsigned)__double2loint(d);
+  const int mx = hx & 0x7fffffff, md = hd & 0x7fffffff;
+  const bool take_x = mx < md || (mx == md && lx <= ld);
+  const bool opposite = (hx ^ hd) < 0;
+  const int rh = opposite ? 0 : (take_x ? hx : hd);
+  const unsigned rl = opposite ? 0u : (take_x ? lx : ld);
+  return __hiloint2double(rh, (int)rl);
 }
 
 // dx * d(v f)/dx / v along one axis, from the upwind-side stencil:
