@@ -27,6 +27,8 @@ CASES = {
     "line_2x1x1_extrapolate": dict(n=(2, 1, 1), lo=(2, 0, 0), hi=(2, 0, 0), c=(2.0, 6.0, 2.0)),
     "column_1x5x3": dict(n=(1, 5, 3), lo=(0, 3, 1), hi=(0, 3, 1), c=(2.0, 5.0, 2.5)),
     "wide_70x9x5": dict(n=(70, 9, 5), lo=(1, 0, 3), hi=(1, 0, 3), c=(2.0, 6.0, 2.0)),
+    # nx, ny multiples of both tile shapes (32 x 8, 64 x 8): the pair kernels' full-tile form
+    "full_tiles_64x16x10": dict(n=(64, 16, 10), lo=(1, 0, 3), hi=(2, 0, 3), c=(2.0, 6.0, 4.0)),
 }
 
 

@@ -62,6 +62,37 @@ def test_fp32_step_parity(name, variant):
     assert err.max() <= FP32_TOL, err
 
 
+@pytest.mark.parametrize("dt_equals_tau", [False, True])
+def test_fp32_full_tile_and_dt_tau_forms(dt_equals_tau):
+    """On a grid of whole tiles the pair kernels take their full-tile form,
+    and with dt = tau also the form whose diagonal update is f^eq itself:
+    parity with the oracle, and bitwise equality with the field-split kernel
+    (which has neither) and with the same grid stepped in a batch."""
+    from paper_1010_4135_gb300 import sim as S
+    cfg = case_cfg("full_tiles_64x16x10", dt=2e-4, tau=2e-4 if dt_equals_tau else 5e-4)
+    f0 = initial_f(cfg, seed=21).astype(np.float32)
+    res = {}
+    for v in ("tiled", "tiled64", "split"):
+        s = sim_for(cfg, "fp32")
+        s.set_launch(v)
+        s.set_f(f0)
+        s.step(STEPS)
+        res[v] = s.get_f()
+    ref = oracle.run(cfg, f0.astype(np.float64), STEPS, NTHREADS)
+    assert field_errors(res["tiled"], ref).max() <= FP32_TOL
+    assert np.array_equal(res["tiled"], res["tiled64"])
+    assert np.array_equal(res["tiled"], res["split"])
+    # two such grids in one batched launch take the batched kernel's full-tile (and dt = tau) form
+    pair = []
+    for _ in range(2):
+        s = sim_for(cfg, "fp32")
+        s.set_f(f0)
+        pair.append(s)
+    S.step_batch(pair, STEPS)
+    for s in pair:
+        assert np.array_equal(s.get_f(), res["tiled"])
+
+
 @pytest.mark.parametrize("variant", ["tiled", "tiled64", "split", "tiled_single"])
 @pytest.mark.parametrize("scheme", [oracle.UPWIND2, oracle.UPWIND1])
 def test_fp32_tiled_other_schemes(scheme, variant):
