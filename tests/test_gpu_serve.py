@@ -74,3 +74,28 @@ def test_unhealthy_results_are_solved_again_with_the_next_parameters(monkeypatch
         alone, _, _ = s.moments()
         assert np.array_equal(alone, j.rho)
     assert serve.summary(done, srv.wall)["retried"] == len(tr)
+
+
+def test_served_fp32_result_against_the_oracle():
+    """A served 64^3 request (parameters from the on-device rule) against the
+    oracle itself, not the FP64 path: its FP32 density after the request's
+    steps is within the FP32 error model's bound, kappa taken over the
+    request's states and the star states where the shocked gas meets the
+    second gas (parity_util.fp32_l1_bound)."""
+    import oracle
+    from paper_1010_4135_gb300 import serve, stability
+    from parity_util import NTHREADS, fp32_l1_bound, l1_rel, linf_rel
+    tr = workloads.serving_trace(seed=11, n=2, rate=200.0, grids=((64, 64, 64),), steps=(400, 500))
+    srv = serve.Server(max_batch=2, tick=16, keep_results=True)
+    done = srv.run(tr)
+    assert len(done) == 2 and all(j.health == 0 for j in done)
+    j = min(done, key=lambda d: d.req["id"])  # one request: 1.2e8 cell-updates for the oracle
+    w = workloads.request_workload(j.req, *j.params)
+    cfg = oracle.cfg_for(w)
+    f = oracle.run(cfg, oracle.init(cfg, *w.initial_fields()), j.req["steps"], NTHREADS)
+    ro, _, _ = oracle.macros(cfg, f)
+    pre, post, other = workloads.request_states(j.req)
+    bound = fp32_l1_bound(cfg, [pre, post, other, *stability.interaction_states(post, other)], j.req["steps"])
+    print(f"served {j.req['kind']} 64^3 Mach {j.req['mach']:.2f} ratio {j.req['ratio']:.2f} fp32 vs oracle after "
+          f"{j.req['steps']} steps: L1 {l1_rel(j.rho, ro):.3e} Linf {linf_rel(j.rho, ro):.3e} (model bound {bound:.2e})")
+    assert l1_rel(j.rho, ro) <= bound
