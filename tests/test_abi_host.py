@@ -156,3 +156,16 @@ def test_external_faces_are_x_faces_of_two_cells_or_more(A):
 def test_every_bound_entry_point_has_a_forwarder(A):
     for n, _, _ in A.SIGNATURES:
         assert callable(getattr(A, n, None)), n
+
+
+def test_diagnostic_entry_points_check_their_arguments_before_any_device_call(A):
+    p = ctypes.c_void_p(256)
+    assert A.lbm_reciprocal_fp32(None, None, 0, None) == A.LBM_OK      # nothing to do, nothing launched
+    assert A.lbm_reciprocal_fp32(p, p, -1, None) == A.LBM_EINVAL
+    assert A.lbm_reciprocal_fp32(None, p, 4, None) == A.LBM_EINVAL
+    assert A.lbm_reciprocal_fp32(p, None, 4, None) == A.LBM_EINVAL
+    assert A.lbm_vn_max_growth(p, 0, p, 1, p, 1, 8, 1, p, None) == A.LBM_EINVAL
+    assert A.lbm_vn_max_growth(p, 1, p, 1, p, 1, 8, 1, None, None) == A.LBM_EINVAL
+    # 2^31 matrices in one call, more than the 2^30 allowed (every call here is
+    # refused before anything reaches a device: the pointers are not real)
+    assert A.lbm_vn_max_growth(p, 1 << 11, p, 1 << 10, p, 4, 256, 1, p, None) == A.LBM_EINVAL
