@@ -452,13 +452,21 @@ def run_ours(args):
         oT = torch.empty_like(hT).pin_memory()
         import ctypes
         from paper_1010_4135_gb300 import _abi as A
+
+        def e2e_pass(nsteps):
+            A.check(A.lbm_init(s.handle, ctypes.c_void_p(hr.data_ptr()), ctypes.c_void_p(hu.data_ptr()),
+                               ctypes.c_void_p(hT.data_ptr()), 0), "lbm_init")
+            A.check(A.lbm_step(s.handle, nsteps), "lbm_step")
+            A.check(A.lbm_moments(s.handle, ctypes.c_void_p(orho.data_ptr()), ctypes.c_void_p(ou.data_ptr()),
+                                  ctypes.c_void_p(oT.data_ptr()), 0), "lbm_moments")
+
+        # one untimed pass (the warm-up step count): the first transfers from
+        # freshly pinned buffers map their pages and ran at a fraction of the
+        # link's rate
+        e2e_pass(args.warmup)
         barrier()
         t0e = time.perf_counter()
-        A.check(A.lbm_init(s.handle, ctypes.c_void_p(hr.data_ptr()), ctypes.c_void_p(hu.data_ptr()),
-                           ctypes.c_void_p(hT.data_ptr()), 0), "lbm_init")
-        A.check(A.lbm_step(s.handle, args.steps), "lbm_step")
-        A.check(A.lbm_moments(s.handle, ctypes.c_void_p(orho.data_ptr()), ctypes.c_void_p(ou.data_ptr()),
-                              ctypes.c_void_p(oT.data_ptr()), 0), "lbm_moments")
+        e2e_pass(args.steps)
         te = time.perf_counter() - t0e
         te, _ = replicas.aggregate(te, 0, device=torch.device("cuda", dev))
         io = (hr.numel() + hu.numel() + hT.numel()) * 8
