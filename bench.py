@@ -472,7 +472,8 @@ def run_ours(args):
         io = (hr.numel() + hu.numel() + hT.numel()) * 8
         e2e = {"value": total_cells / te, "unit": UNIT,
                "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
-               "note": "per run: lbm_init from pinned host (rho,u,T) + steps + lbm_moments to pinned host"}
+               "note": "per run: lbm_init from pinned host (rho,u,T) + steps + lbm_moments to pinned host, "
+                       "after one untimed pass of the same sequence with the warm-up step count"}
 
     # FP32 density error of a run of args.steps steps against the FP64 path
     accuracy = None
